@@ -1,0 +1,324 @@
+"""Benchmark of the GB300 DNA automaton scan (one JSON line on rank 0).
+
+Workload (default): the plain scan of a 256 MiB order-2 Markov A/C/G/T sequence
+(41% GC, seed 1) with the minimal DFA of ACG[AT]{2,6}C(G|T)T, returning the exact count
+and all match positions. A step is one dna_scan call over the whole sequence: ingest,
+speculation, chunk scan, join/repair and position extraction. The input (256 MiB) is
+larger than L2 (129 MB), so consecutive steps do not hit a warm cache.
+
+Arms:
+  default            the library (CUDA kernels through the C ABI);
+  --impl reference   the CPU oracle (plain single-threaded C) on a bounded sample of
+                     the same workload, timed on the host cores.
+Under torchrun (N > 1) every rank scans its own sequence (independent problems, no
+collective): weak scaling, value = all ranks' bytes / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MiB = 1 << 20
+METRIC = "sequence GB/s scanned (count + positions)"
+WORKLOAD = ("plain scan: 256 MiB order-2 Markov A/C/G/T (41% GC, seed 1), minimal DFA of "
+            "ACG[AT]{2,6}C(G|T)T, exact count + all match positions")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--bytes", type=int, default=256 * MiB)
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("paper_1509_01506_gb300/csrc/dna_scan.cu",):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the scan kernel from the committed ncu summary, or None
+    when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "scan_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(rec["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def cpu_oracle_rate(seq: np.ndarray, pattern: str, seconds: float):
+    """The oracle (single-threaded C) on consecutive 32 MiB slices of the workload until
+    'seconds' have elapsed; returns (GB/s, bytes scanned)."""
+    import oracle
+    t, a = oracle.compile_regex(pattern)
+    slice_bytes = 32 * MiB
+    done, t0 = 0, time.perf_counter()
+    i = 0
+    while True:
+        lo = (i * slice_bytes) % seq.size
+        part = seq[lo:lo + slice_bytes]
+        oracle.run(t, a, part, positions=True, cap=1 << 16)
+        done += part.size
+        i += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return done / el / 1e9, done
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    n = min(args.bytes, 64 * MiB)
+    seq, pattern = synth.plain_markov(args.bytes)
+    seq = seq[:n]
+    import oracle
+    t, a = oracle.compile_regex(pattern)
+    for _ in range(args.warmup):
+        oracle.run(t, a, seq[:MiB], positions=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(t, a, seq, positions=True, cap=1 << 16)
+    el = time.perf_counter() - t0
+    gbs = n * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "bytes_per_step": n,
+                                        "sample": f"first {n // MiB} MiB of the workload per step"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n // MiB} MiB of the 256 MiB sequence per step"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1509_01506_gb300 as dna
+    import synth
+
+    seq_np, pattern = synth.plain_markov(args.bytes)
+    n = seq_np.size
+    dfa = dna.Dfa.from_regex(pattern)
+    dseq = torch.from_numpy(seq_np).cuda()
+    cap = 1 << 20
+    out_count = torch.empty(1, dtype=torch.int64, device="cuda")
+    out_pos = torch.empty(cap, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dna.scan(dfa, dseq, positions=True, stream=stream, out_count=out_count,
+                 out_positions=out_pos, capacity=cap)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_matches = int(out_count.item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.3)
+    dna.profile_read(reset=True)
+    dna.profile_enable(True)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    dna.profile_enable(False)
+    prof = dna.profile_read(reset=True)
+    clocks = sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = n * world / (ms_step * 1e-3) / 1e9
+
+    # ---- end to end: pinned host input -> device -> scan -> count + positions to host
+    host_in = torch.from_numpy(seq_np).pin_memory()
+    host_count = torch.empty(1, dtype=torch.int64).pin_memory()
+    host_pos = torch.empty(cap, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, args.e2e_steps)
+
+    def e2e_step():
+        dseq.copy_(host_in, non_blocking=True)
+        dna.scan(dfa, dseq, positions=True, stream=stream, out_count=out_count,
+                 out_positions=out_pos, capacity=cap)
+        host_count.copy_(out_count, non_blocking=True)
+        host_pos[:n_matches].copy_(out_pos[:n_matches], non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    assert int(host_count.item()) == n_matches
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = n * world / (e2e_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the chunk scan), timed live with events
+    peak, peak_kind = load_peaks()
+    kms = prof["scan_kernel_ms"] / max(1, prof["scan_kernel_calls"])
+    achieved = n / (kms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": n, "kernel_ms": kms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done = cpu_oracle_rate(seq_np, pattern, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done / MiB:.0f} MiB scanned as 32 MiB slices of the 256 MiB workload "
+                         f"(count + positions), single thread"}
+
+    info = dfa.info()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "bytes_per_gpu": n, "n_states": info.n_states,
+                       "definite_depth": info.definite_depth, "lookback": info.lookback,
+                       "placement": info.placement, "matches": n_matches,
+                       "l2": "inputs larger than L2 (256 MiB > 129 MB), no flush",
+                       "parallelism": f"independent sequences on {world} GPU(s)",
+                       "e2e_steps": e2e_steps},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": n,
+                    "d2h_bytes_per_step": 8 + 8 * n_matches},
+            "gpu_launches": prof["kernel_launches"],
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * dna_dfa.h -- C ABI of the GB300 DNA automaton scan library (libdnadfa.so).
+ *
+ * The library runs a deterministic finite automaton over a DNA byte sequence on one
+ * GPU, following Memeti & Pllana, "Analyzing large-scale DNA Sequences on Multi-core
+ * Architectures" (CSE 2015):
+ *   - the automaton is the quintuple (Q, Sigma, delta, q0, F) of Sec. II, over the
+ *     alphabet A, C, G, T, with q0 = state 0;
+ *   - the input is split into chunks (input-based partitioning, Sec. III-A, Fig. 1a);
+ *     each chunk's unknown start state is speculated from the symbols before it
+ *     (the possible-starting-state idea of Sec. III-A), every chunk is scanned in
+ *     parallel, and a join links each chunk's last state to the next chunk's first
+ *     state (the "binary reduction" of Sec. III-A); a wrong speculation is repaired
+ *     at the converging point (Sec. III-B.3, Alg. 1), where a run from the true state
+ *     meets the speculative run after the same number of symbols;
+ *   - the result is the exact count of match end positions and, optionally, the
+ *     positions themselves (Sec. III-A: counting and extracting k-mers).
+ *
+ * Semantics every entry point shares (the definition the results must equal):
+ *   Each byte is one symbol. A/a, C/c, G/g, T/t are the four bases; any other byte
+ *   (N, IUPAC codes, newline, ...) is a reset symbol that sends every state to state
+ *   0. The scan starts in state 0, takes one transition per byte and tests the
+ *   post-transition state against F (Alg. 1 tests the state after each transition).
+ *   The count is the number of such steps that land in F; the positions are the
+ *   0-based byte indices of those steps, strictly ascending. For a compiled pattern
+ *   this reports every j such that some non-empty substring ending at j, with no
+ *   reset byte inside, is a word of the pattern (overlapping occurrences included,
+ *   Sec. II).
+ *
+ * Threading and ownership: handles may be used from several host threads at once;
+ * calls on different streams may overlap. The caller owns every sequence and output
+ * buffer. Device results are written asynchronously on the given stream and are
+ * valid once the stream has completed the call's work.
+ *
+ * Errors: every entry point returns DNA_OK (0) or a negative DNA_ERR_* code.
+ * Argument errors are detected before any work is queued and leave outputs untouched.
+ */
+#ifndef DNA_DFA_H
+#define DNA_DFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA headers. 0 = the legacy default stream. */
+typedef struct CUstream_st *dna_stream_t;
+
+#define DNA_OK                 0
+#define DNA_ERR_INVALID_ARG   -1  /* null pointer, n_states = 0, entry >= n_states, bad size */
+#define DNA_ERR_NOMEM         -2  /* a host or device allocation failed */
+#define DNA_ERR_CAPACITY      -3  /* a fixed capacity (states, batch shape) was exceeded */
+#define DNA_ERR_TIMEOUT       -4  /* a bounded device wait gave up (status word) */
+#define DNA_ERR_CUDA          -5  /* a CUDA runtime call failed */
+#define DNA_ERR_SYNTAX        -6  /* pattern syntax error (host compiler) */
+#define DNA_ERR_EMPTY_WORD    -7  /* pattern language contains the empty word */
+#define DNA_ERR_NO_DEVICE     -8  /* no usable CUDA device / wrong architecture */
+
+typedef struct dna_dfa dna_dfa; /* opaque; its tables live in device memory */
+
+/*
+ * dfa_load -- copies a complete DFA to the current CUDA device (Sec. II quintuple).
+ *   table       host, row-major uint32 [n_states][4], columns A, C, G, T; every entry
+ *               < n_states. State 0 is q0 and the target of the reset symbol.
+ *   n_states    1 .. 2^24.
+ *   accept_mask host, bit-packed: bit (q % 8) of byte q / 8 set <=> q in F;
+ *               ceil(n_states / 8) bytes.
+ *   out         receives the handle; the library owns it until dfa_free.
+ * The table is copied (the caller may free its buffers on return). dfa_load also
+ * analyses the automaton on the host (its definite depth: the smallest m such that
+ * any m symbols bring every state to one state, when m <= 64) and picks the
+ * speculation lookback and the table placement used by the scans.
+ * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_NOMEM, DNA_ERR_CUDA, DNA_ERR_NO_DEVICE.
+ */
+int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t *accept_mask,
+             dna_dfa **out);
+
+/* dfa_free -- releases a handle (NULL is ignored). No scan using it may be in flight. */
+void dfa_free(dna_dfa *dfa);
+
+typedef struct {
+    uint32_t n_states;
+    int32_t  definite_depth;   /* m, or -1 when not m-definite for any m <= 64 */
+    uint32_t lookback;         /* symbols read before each chunk to speculate its start */
+    uint32_t placement;        /* DNA_PLACE_* chosen for this automaton */
+    uint32_t accept_start;     /* 1 when state 0 is in F */
+    int32_t  device;
+} dna_dfa_info;
+
+#define DNA_PLACE_AUTO       0
+#define DNA_PLACE_SMEM_PAIR  1  /* two-symbol table, one copy per lane, shared memory */
+#define DNA_PLACE_SMEM_ONE   2  /* one-symbol table in shared memory */
+#define DNA_PLACE_GLOBAL_ONE 3  /* one-symbol table in global memory (L2 resident) */
+
+int dfa_info(const dna_dfa *dfa, dna_dfa_info *out);
+
+/*
+ * dfa_analyze -- host-only analysis of a table in the dfa_load layout (no GPU needed).
+ * Writes the definite depth m (the smallest m such that every word of m symbols sends
+ * all states to one state, so m symbols before a chunk fix its start state exactly;
+ * Sec. III-B.3's converging point reached from every start), or -1 when the table is
+ * not m-definite for any m <= 64 or has more than 4096 states (the analysis is
+ * quadratic in the state count). Errors: DNA_ERR_INVALID_ARG, DNA_ERR_NOMEM.
+ */
+int dfa_analyze(const uint32_t *table, uint32_t n_states, int32_t *definite_depth);
+
+/*
+ * dna_scan -- scans one device sequence with one automaton (the plain path).
+ *   seq            device pointer to len bytes (any alignment); may be NULL if len = 0.
+ *   len            number of bytes (0 .. 2^40).
+ *   stream         CUDA stream the work is queued on.
+ *   out_count      device or host-mapped pointer; receives the exact count.
+ *   out_positions  device pointer or NULL. When non-NULL, receives the first
+ *                  min(count, positions_capacity) match positions (uint64, ascending).
+ *                  A count above positions_capacity is visible as *out_count >
+ *                  positions_capacity; the written positions are then the smallest
+ *                  positions_capacity ones.
+ *   positions_capacity  number of uint64 slots at out_positions.
+ * Scratch: the call allocates stream-ordered device scratch (cudaMallocAsync) sized
+ * O(len / chunk) and frees it on the same stream.
+ * Errors: DNA_ERR_INVALID_ARG (synchronous), DNA_ERR_NOMEM, DNA_ERR_CUDA.
+ */
+int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t stream,
+             uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity);
+
+/*
+ * Plan override for dna_scan_planned (tests sweep it: results must not depend on it).
+ *   chunk_bytes    bytes per chunk (one chunk per GPU lane); multiple of 128, >= 128;
+ *                  0 = automatic.
+ *   lookback       symbols read before a chunk to speculate its start state
+ *                  (1 = the paper's possible starting states from one symbol);
+ *                  0 = automatic; at most 64.
+ *   warps_per_cta  4, 8 or 16; 0 = automatic.
+ *   placement      DNA_PLACE_*; 0 = automatic. A placement the automaton does not fit
+ *                  in returns DNA_ERR_CAPACITY.
+ */
+typedef struct {
+    uint32_t chunk_bytes;
+    uint32_t lookback;
+    uint32_t warps_per_cta;
+    uint32_t placement;
+} dna_plan;
+
+int dna_scan_planned(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
+                     dna_stream_t stream, uint64_t *out_count, uint64_t *out_positions,
+                     uint64_t positions_capacity, const dna_plan *plan);
+
+/*
+ * dna_scan_batch -- counts every (sequence, automaton) pair of a batch in one queued
+ * launch sequence (the batched path).
+ *   dfas     host array of n_dfas handles (all loaded on the current device).
+ *   seqs     host array of n_seqs device pointers; lens host array of their lengths.
+ *   out_counts device uint64 [n_seqs][n_dfas], row-major; element (s, d) receives the
+ *            count of automaton d over sequence s.
+ * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_NOMEM, DNA_ERR_CUDA, DNA_ERR_CAPACITY.
+ */
+int dna_scan_batch(const dna_dfa *const *dfas, uint32_t n_dfas,
+                   const uint8_t *const *seqs, const uint64_t *lens, uint32_t n_seqs,
+                   dna_stream_t stream, uint64_t *out_counts);
+
+/* dna_status_string -- a static description of a status code. */
+const char *dna_status_string(int status);
+
+/*
+ * Host pattern compilers (convenience; no GPU needed). They return the minimal
+ * complete DFA of Sigma*.L with canonical breadth-first numbering (state 0 = start),
+ * in the dfa_load layout. *table_out and *accept_out are allocated by the library;
+ * release them with dna_free_host.
+ *   dna_compile_regex: syntax A C G T (case-insensitive), '.', [classes], ( ), |,
+ *     * + ? {n} {n,} {n,m}; a pattern matching the empty word is rejected.
+ *   dna_compile_kmers: Aho-Corasick automaton of n base strings (Sec. II; the
+ *     failure-free form of Sec. III-B.1), minimised the same way.
+ * Errors: DNA_ERR_SYNTAX, DNA_ERR_EMPTY_WORD, DNA_ERR_INVALID_ARG, DNA_ERR_CAPACITY,
+ * DNA_ERR_NOMEM.
+ */
+int dna_compile_regex(const char *pattern, uint32_t **table_out, uint8_t **accept_out,
+                      uint32_t *n_states_out);
+int dna_compile_kmers(const char *const *kmers, uint32_t n_kmers, uint32_t **table_out,
+                      uint8_t **accept_out, uint32_t *n_states_out);
+void dna_free_host(void *p);
+
+/*
+ * Profiling hooks (bench and tests). When enabled, every scan records CUDA events
+ * around its chunk-scan kernel on the caller's stream; dna_profile_read synchronises
+ * those events and returns the accumulated kernel time and the number of kernels
+ * this library launched since the last reset.
+ */
+typedef struct {
+    double   scan_kernel_ms;    /* summed duration of the chunk-scan kernel */
+    uint64_t scan_kernel_calls;
+    uint64_t kernel_launches;   /* all kernels launched by the library */
+} dna_profile_t;
+
+void dna_profile_enable(int enable);
+int  dna_profile_read(dna_profile_t *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DNA_DFA_H */

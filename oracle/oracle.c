@@ -216,6 +216,7 @@ static int rx_rep(rx_parser *ps)
                 }
             } else { ps->err = OR_ERR_SYNTAX; return -1; }
             if (ps->err) return -1;
+            if (hi == 0) { ps->err = OR_ERR_SYNTAX; return -1; } /* zero-width repeat */
         } else break;
         int r = rx_new(ps, RX_REP);
         if (r < 0) return -1;

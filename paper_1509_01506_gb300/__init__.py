@@ -1,0 +1,296 @@
+"""Python binding of libdnadfa.so (the C ABI declared in include/dna_dfa.h).
+
+Argument marshalling only: every step of a scan runs in the library's CUDA kernels.
+PyTorch provides device memory and streams. There is no CPU fallback: if the shared
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+DNA_OK = 0
+PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE = 0, 1, 2, 3
+
+EXPORTED = [
+    "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
+    "dna_status_string", "dna_compile_regex", "dna_compile_kmers", "dna_free_host",
+    "dna_profile_enable", "dna_profile_read",
+]
+
+
+class DnaError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = status_string(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_uint32), ("definite_depth", ctypes.c_int32),
+                ("lookback", ctypes.c_uint32), ("placement", ctypes.c_uint32),
+                ("accept_start", ctypes.c_uint32), ("device", ctypes.c_int32)]
+
+
+class _Plan(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_uint32), ("lookback", ctypes.c_uint32),
+                ("warps_per_cta", ctypes.c_uint32), ("placement", ctypes.c_uint32)]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("scan_kernel_ms", ctypes.c_double), ("scan_kernel_calls", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64)]
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIBPATH
+
+
+def lib():
+    """Loads libdnadfa.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIBPATH):
+            raise RuntimeError(f"libdnadfa.so not found at {_build.LIBPATH}; run build()")
+        L = ctypes.CDLL(_build.LIBPATH)
+        p, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        L.dfa_load.argtypes = [p, u32, p, ctypes.POINTER(p)]
+        L.dfa_load.restype = i32
+        L.dfa_free.argtypes = [p]
+        L.dfa_free.restype = None
+        L.dfa_info.argtypes = [p, ctypes.POINTER(_Info)]
+        L.dfa_info.restype = i32
+        L.dfa_analyze.argtypes = [p, u32, ctypes.POINTER(ctypes.c_int32)]
+        L.dfa_analyze.restype = i32
+        L.dna_scan.argtypes = [p, p, u64, p, p, p, u64]
+        L.dna_scan.restype = i32
+        L.dna_scan_planned.argtypes = [p, p, u64, p, p, p, u64, ctypes.POINTER(_Plan)]
+        L.dna_scan_planned.restype = i32
+        L.dna_scan_batch.argtypes = [p, u32, p, p, u32, p, p]
+        L.dna_scan_batch.restype = i32
+        L.dna_status_string.argtypes = [i32]
+        L.dna_status_string.restype = ctypes.c_char_p
+        L.dna_compile_regex.argtypes = [ctypes.c_char_p, ctypes.POINTER(p), ctypes.POINTER(p),
+                                        ctypes.POINTER(u32)]
+        L.dna_compile_regex.restype = i32
+        L.dna_compile_kmers.argtypes = [p, u32, ctypes.POINTER(p), ctypes.POINTER(p),
+                                        ctypes.POINTER(u32)]
+        L.dna_compile_kmers.restype = i32
+        L.dna_free_host.argtypes = [p]
+        L.dna_free_host.restype = None
+        L.dna_profile_enable.argtypes = [i32]
+        L.dna_profile_enable.restype = None
+        L.dna_profile_read.argtypes = [ctypes.POINTER(_Profile), i32]
+        L.dna_profile_read.restype = i32
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    return lib().dna_status_string(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != DNA_OK:
+        raise DnaError(rc, what)
+
+
+# ------------------------------------------------------------------ compilers
+
+def _take_table(tp, ap, n):
+    L = lib()
+    try:
+        table = np.ctypeslib.as_array(ctypes.cast(tp, ctypes.POINTER(ctypes.c_uint32)),
+                                      shape=(n, 4)).copy()
+        mask = np.ctypeslib.as_array(ctypes.cast(ap, ctypes.POINTER(ctypes.c_uint8)),
+                                     shape=((n + 7) // 8,)).copy()
+    finally:
+        L.dna_free_host(tp)
+        L.dna_free_host(ap)
+    return table, mask
+
+
+def compile_regex(pattern: str):
+    """Host compiler: (table uint32 [Q,4] columns A,C,G,T; bit-packed accept mask)."""
+    tp, ap, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_uint32()
+    _check(lib().dna_compile_regex(pattern.encode(), ctypes.byref(tp), ctypes.byref(ap),
+                                   ctypes.byref(n)), f"compile_regex({pattern!r})")
+    return _take_table(tp, ap, n.value)
+
+
+def compile_kmers(kmers):
+    arr = (ctypes.c_char_p * len(kmers))(*[k.encode() for k in kmers])
+    tp, ap, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_uint32()
+    _check(lib().dna_compile_kmers(ctypes.cast(arr, ctypes.c_void_p), len(kmers),
+                                   ctypes.byref(tp), ctypes.byref(ap), ctypes.byref(n)),
+           "compile_kmers")
+    return _take_table(tp, ap, n.value)
+
+
+def definite_depth(table) -> int:
+    """Host-only analysis (dfa_analyze): definite depth, or -1."""
+    t = np.ascontiguousarray(table, dtype=np.uint32)
+    m = ctypes.c_int32()
+    _check(lib().dfa_analyze(t.ctypes.data, t.shape[0], ctypes.byref(m)), "dfa_analyze")
+    return m.value
+
+
+def pack_accept(accept) -> np.ndarray:
+    """0/1 per state -> the bit-packed mask dfa_load takes."""
+    a = np.asarray(accept).astype(bool)
+    return np.packbits(a, bitorder="little")
+
+
+# ----------------------------------------------------------------- automata
+
+@dataclass
+class DfaInfo:
+    n_states: int
+    definite_depth: int
+    lookback: int
+    placement: int
+    accept_start: bool
+    device: int
+
+
+class Dfa:
+    """A device-resident automaton (dfa_load / dfa_free)."""
+
+    def __init__(self, table, accept_mask):
+        table = np.ascontiguousarray(table, dtype=np.uint32)
+        mask = np.ascontiguousarray(accept_mask, dtype=np.uint8)
+        if table.ndim != 2 or table.shape[1] != 4:
+            raise ValueError("table must be [n_states, 4]")
+        n = table.shape[0]
+        if mask.size < (n + 7) // 8:
+            raise ValueError("accept mask too short")
+        h = ctypes.c_void_p()
+        _check(lib().dfa_load(table.ctypes.data, n, mask.ctypes.data, ctypes.byref(h)), "dfa_load")
+        self._h = h
+        self.table = table
+        self.accept_mask = mask
+
+    @classmethod
+    def from_regex(cls, pattern: str) -> "Dfa":
+        return cls(*compile_regex(pattern))
+
+    @classmethod
+    def from_kmers(cls, kmers) -> "Dfa":
+        return cls(*compile_kmers(list(kmers)))
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("automaton was freed")
+        return self._h.value
+
+    def info(self) -> DfaInfo:
+        i = _Info()
+        _check(lib().dfa_info(self.handle, ctypes.byref(i)), "dfa_info")
+        return DfaInfo(i.n_states, i.definite_depth, i.lookback, i.placement,
+                       bool(i.accept_start), i.device)
+
+    def free(self):
+        if self._h:
+            lib().dfa_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------- scans
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def scan(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None,
+         stream=None, plan: dict | None = None, out_count=None, out_positions=None):
+    """dna_scan on a CUDA uint8 tensor. Returns (count tensor [1] uint64-as-int64,
+    positions tensor or None). Results are ready when the stream completes."""
+    import torch
+    if not (isinstance(seq, torch.Tensor) and seq.is_cuda and seq.dtype == torch.uint8):
+        raise TypeError("seq must be a CUDA uint8 tensor")
+    if not seq.is_contiguous():
+        raise ValueError("seq must be contiguous")
+    dev = seq.device
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=dev)
+    pos_ptr, cap = None, 0
+    if positions:
+        if out_positions is None:
+            cap = int(capacity if capacity is not None else max(1024, seq.numel() // 256))
+            out_positions = torch.empty(cap, dtype=torch.int64, device=dev)
+        else:
+            cap = out_positions.numel() if capacity is None else int(capacity)
+        pos_ptr = out_positions.data_ptr()
+    sh = _stream_handle(stream)
+    L = lib()
+    if plan:
+        pl = _Plan(plan.get("chunk_bytes", 0), plan.get("lookback", 0),
+                   plan.get("warps_per_cta", 0), plan.get("placement", 0))
+        rc = L.dna_scan_planned(dfa.handle, seq.data_ptr(), seq.numel(), sh,
+                                out_count.data_ptr(), pos_ptr, cap, ctypes.byref(pl))
+    else:
+        rc = L.dna_scan(dfa.handle, seq.data_ptr(), seq.numel(), sh, out_count.data_ptr(),
+                        pos_ptr, cap)
+    _check(rc, "dna_scan")
+    return out_count, (out_positions if positions else None)
+
+
+def scan_ptr(dfa: Dfa, ptr: int, length: int, out_count_ptr: int, stream_handle: int,
+             positions_ptr: int | None = None, capacity: int = 0) -> None:
+    """Raw-pointer form of dna_scan (device or host-mapped pointers)."""
+    _check(lib().dna_scan(dfa.handle, ptr, length, stream_handle, out_count_ptr,
+                          positions_ptr, capacity), "dna_scan")
+
+
+def scan_batch(dfas, seqs, stream=None, out=None):
+    """dna_scan_batch: counts [n_seqs, n_dfas] (int64 tensor) for CUDA uint8 tensors."""
+    import torch
+    n_d, n_s = len(dfas), len(seqs)
+    dev = seqs[0].device
+    hs = (ctypes.c_void_p * n_d)(*[d.handle for d in dfas])
+    ptrs = (ctypes.c_void_p * n_s)(*[s.data_ptr() for s in seqs])
+    lens = (ctypes.c_uint64 * n_s)(*[s.numel() for s in seqs])
+    if out is None:
+        out = torch.empty((n_s, n_d), dtype=torch.int64, device=dev)
+    _check(lib().dna_scan_batch(ctypes.cast(hs, ctypes.c_void_p), n_d,
+                                ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(lens, ctypes.c_void_p),
+                                n_s, _stream_handle(stream), out.data_ptr()), "dna_scan_batch")
+    return out
+
+
+def profile_enable(on: bool = True):
+    lib().dna_profile_enable(1 if on else 0)
+
+
+def profile_read(reset: bool = False) -> dict:
+    pr = _Profile()
+    _check(lib().dna_profile_read(ctypes.byref(pr), 1 if reset else 0), "dna_profile_read")
+    return {"scan_kernel_ms": pr.scan_kernel_ms, "scan_kernel_calls": pr.scan_kernel_calls,
+            "kernel_launches": pr.kernel_launches}

@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit-exact for
+counts and positions, on seeded synthetic inputs that span many chunks and tiles and
+end in a ragged tail, plus the edge cases of the method (resets, unaligned starts,
+non-converging automata, capacity limits)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1509_01506_gb300 as dna
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MiB = 1 << 20
+
+
+def oracle_tables(kind, pat):
+    if kind == "regex":
+        return oracle.compile_regex(pat)
+    return oracle.compile_kmers(pat, minimise=True)
+
+
+def lib_dfa(kind, pat):
+    return dna.Dfa.from_regex(pat) if kind == "regex" else dna.Dfa.from_kmers(pat)
+
+
+def to_device(seq: np.ndarray, offset: int = 0):
+    """Copies seq to the GPU so that its first byte sits 'offset' bytes past a 256-byte
+    aligned allocation (exercises unaligned starts)."""
+    buf = torch.empty(seq.size + offset + 16, dtype=torch.uint8, device="cuda")
+    view = buf[offset:offset + seq.size]
+    view.copy_(torch.from_numpy(seq))
+    return view
+
+
+def gpu_run(dfa, dseq, positions=True, capacity=None, plan=None):
+    cnt, pos = dna.scan(dfa, dseq, positions=positions, capacity=capacity, plan=plan)
+    torch.cuda.synchronize()
+    c = int(cnt.item())
+    if not positions:
+        return c, None
+    k = min(c, pos.numel())
+    return c, pos[:k].cpu().numpy()
+
+
+def check(kind, pat, seq, offset=0, plan=None, positions=True):
+    t, a = oracle_tables(kind, pat)
+    want_c, want_p = oracle.run(t, a, seq, positions=positions)
+    dfa = lib_dfa(kind, pat)
+    c, p = gpu_run(dfa, to_device(seq, offset), positions=positions,
+                   capacity=max(16, want_c + 5), plan=plan)
+    assert c == want_c
+    if positions:
+        assert np.array_equal(p, want_p)
+    return c
+
+
+def noisy_markov(seed, n, n_frac=0.01, lower_frac=0.1):
+    s = synth.markov2(seed, n)
+    synth.overlay_runs(s, seed, lower_frac, 300.0, "lower")
+    synth.overlay_runs(s, seed + 1, n_frac, 200.0, "N")
+    return s
+
+
+# ------------------------------------------------------------- hand examples
+
+def test_hand_examples_on_gpu():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.tsv")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kind, pats, seq, exp, _ = line.rstrip("\n").split("\t")
+        want = [] if exp == "-" else [int(x) for x in exp.split(",")]
+        pat = pats if kind == "regex" else pats.split(",")
+        dfa = lib_dfa(kind, pat)
+        c, p = gpu_run(dfa, to_device(np.frombuffer(seq.encode(), np.uint8)), capacity=64)
+        assert c == len(want) and p.tolist() == want, (pats, seq)
+
+
+# ------------------------------------------------------- workloads, reduced
+
+def test_plain_small_full_size():
+    """1 MiB uniform, TATAAA (7 states), count + positions."""
+    seq, motif = synth.plain_small()
+    check("regex", motif, seq)
+
+
+def test_plain_markov_reduced():
+    seq = synth.markov2(1, 8 * MiB + 77)
+    check("regex", synth.CONFIG2_REGEX, seq)
+
+
+def test_plain_large_reduced_kmers():
+    """Markov with soft-masked and N runs; AC automaton of 1,000 random 12-mers."""
+    seq = noisy_markov(2, 16 * MiB + 5, n_frac=0.02, lower_frac=0.1)
+    kmers = synth.random_kmers(2, 1000, 12)
+    check("kmers", kmers, seq, positions=True)
+
+
+def test_regex_dna_table_v():
+    seq = noisy_markov(7, 4 * MiB + 3)
+    check("regex", "|".join(synth.REGEX_DNA_TABLE_V), seq)
+
+
+@pytest.mark.parametrize("pattern", synth.random_regexes(3, 12))
+def test_random_motif_regexes(pattern):
+    seq = synth.uniform(11, 1 * MiB + 13)
+    check("regex", pattern, seq)
+
+
+# ------------------------------------------------------ plan independence
+
+PLANS = [
+    dict(chunk_bytes=128, lookback=1, warps_per_cta=4, placement=1),
+    dict(chunk_bytes=256, lookback=3, warps_per_cta=8, placement=1),
+    dict(chunk_bytes=1152, lookback=12, warps_per_cta=16, placement=1),
+    dict(chunk_bytes=8192, lookback=32, warps_per_cta=16, placement=1),
+    dict(chunk_bytes=384, lookback=1, warps_per_cta=8, placement=2),
+    dict(chunk_bytes=640, lookback=5, warps_per_cta=4, placement=3),
+    dict(chunk_bytes=4096, lookback=64, warps_per_cta=16, placement=2),
+]
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "-".join(str(v) for v in p.values()))
+@pytest.mark.parametrize("offset", [0, 5])
+def test_results_do_not_depend_on_the_plan(plan, offset):
+    """Any chunking, lookback (1 = the paper's one-symbol possible starting states),
+    CTA shape or table placement gives the sequential result (Sec. III-A join)."""
+    seq = noisy_markov(5, 3 * MiB + 1001)
+    check("regex", synth.CONFIG2_REGEX, seq, offset=offset, plan=plan)
+
+
+# --------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("n", [0, 1, 2, 15, 16, 17, 127, 128, 129, 4095, 4097, 100003])
+@pytest.mark.parametrize("offset", [0, 1, 7, 15])
+def test_lengths_and_alignment(n, offset):
+    rng = np.random.default_rng(n * 31 + offset)
+    seq = np.frombuffer(b"ACGTN", np.uint8)[rng.integers(0, 5, size=n)].copy() if n else \
+        np.zeros(0, np.uint8)
+    check("regex", "A[CG]T", seq, offset=offset)
+
+
+def test_all_reset_bytes_and_all_byte_values():
+    check("regex", "TATAAA", np.full(50000, ord("N"), np.uint8))
+    rng = np.random.default_rng(1)
+    seq = rng.integers(0, 256, size=300000).astype(np.uint8)
+    bases = np.frombuffer(b"ACGTacgt", np.uint8)
+    pick = rng.random(seq.size) < 0.6
+    seq[pick] = bases[rng.integers(0, 8, size=int(pick.sum()))]
+    check("regex", "A[CG]T", seq)
+    lower = synth.uniform(3, 200000)
+    lower += 32
+    check("regex", "TATA", lower)
+
+
+def test_accepting_start_state_raw_table():
+    """Raw table with state 0 in F: every reset byte is reported."""
+    table = np.array([[1, 0, 0, 0], [1, 1, 0, 0]], dtype=np.uint32)
+    acc = np.array([1, 0], dtype=np.uint8)
+    rng = np.random.default_rng(2)
+    seq = np.frombuffer(b"ACGTN", np.uint8)[rng.integers(0, 5, size=70001)].copy()
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    assert dfa.info().accept_start
+    for plan in (None, dict(chunk_bytes=128, placement=2), dict(chunk_bytes=256, placement=3)):
+        c, p = gpu_run(dfa, to_device(seq, 3), capacity=want_c + 1, plan=plan)
+        assert c == want_c and np.array_equal(p, want_p)
+
+
+def test_single_state_automata():
+    seq = noisy_markov(3, 500000)
+    for acc in (0, 1):
+        table = np.zeros((1, 4), dtype=np.uint32)
+        a = np.array([acc], np.uint8)
+        want_c, _ = oracle.run(table.astype(np.int32), a, seq, positions=False)
+        dfa = dna.Dfa(table, dna.pack_accept(a))
+        c, _ = gpu_run(dfa, to_device(seq), positions=False)
+        assert c == want_c == (seq.size if acc else 0)
+
+
+def test_non_definite_automaton_repair_and_cascade():
+    """A(C|G)*T never converges on runs of C/G: chunks whose speculated start is wrong
+    must be repaired at the converging point or, when the runs never meet, cascaded."""
+    rng = np.random.default_rng(9)
+    parts = []
+    for _ in range(400):
+        parts.append(np.frombuffer(b"CG", np.uint8)[rng.integers(0, 2, size=int(rng.integers(50, 3000)))])
+        parts.append(np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, size=int(rng.integers(1, 30)))])
+    seq = np.concatenate(parts)
+    for plan in (dict(chunk_bytes=128, lookback=1), dict(chunk_bytes=256, lookback=4, placement=2),
+                 dict(chunk_bytes=128, lookback=1, placement=3), None):
+        check("regex", "A(C|G)*T", seq, plan=plan)
+
+
+def test_random_permutation_like_tables():
+    """Random tables are mostly not definite: speculation fails often and the repair /
+    cascade path carries the result."""
+    rng = np.random.default_rng(21)
+    for trial in range(12):
+        Q = int(rng.integers(2, 40))
+        table = rng.integers(0, Q, size=(Q, 4)).astype(np.uint32)
+        if trial % 2 == 0:  # permutations never converge
+            table = np.stack([rng.permutation(Q) for _ in range(4)], axis=1).astype(np.uint32)
+        acc = (rng.random(Q) < 0.3).astype(np.uint8)
+        seq = synth.uniform(100 + trial, 200000 + trial * 17)
+        want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+        dfa = dna.Dfa(table, dna.pack_accept(acc))
+        for plan in (None, dict(chunk_bytes=128, lookback=2, placement=1),
+                     dict(chunk_bytes=512, lookback=1, placement=3)):
+            c, p = gpu_run(dfa, to_device(seq, trial % 16), capacity=want_c + 3, plan=plan)
+            assert c == want_c and np.array_equal(p, want_p), (trial, plan)
+
+
+def test_positions_capacity_smaller_than_count():
+    seq = synth.uniform(5, 2 * MiB)
+    t, a = oracle.compile_regex("AC")
+    want_c, want_p = oracle.run(t, a, seq)
+    dfa = dna.Dfa.from_regex("AC")
+    for cap in (1, 1000, want_c - 1):
+        c, p = gpu_run(dfa, to_device(seq), capacity=cap)
+        assert c == want_c and np.array_equal(p, want_p[:cap])
+
+
+def test_dense_matches_overflow_stash():
+    """'A' matches about a quarter of all positions: every chunk overflows its stash
+    and is rescanned by the extraction pass."""
+    seq = noisy_markov(4, 1 * MiB + 9)
+    check("regex", "A", seq)
+    check("regex", "[ACGT]", seq)
+
+
+def test_large_aho_corasick_placements():
+    seq = noisy_markov(6, 4 * MiB + 1)
+    kmers = synth.random_kmers(6, 1000, 12)
+    for plan in (None, dict(placement=2), dict(placement=3), dict(placement=3, lookback=1)):
+        check("kmers", kmers, seq, plan=plan, positions=True)
+
+
+def test_invalid_arguments_are_rejected():
+    dfa = dna.Dfa.from_regex("ACGT")
+    seq = to_device(synth.uniform(1, 1000))
+    with pytest.raises(dna.DnaError):
+        dna.scan(dfa, seq, plan=dict(chunk_bytes=100))
+    with pytest.raises(dna.DnaError):
+        dna.scan(dfa, seq, plan=dict(lookback=65))
+    with pytest.raises(dna.DnaError):
+        dna.scan(dfa, seq, plan=dict(warps_per_cta=3))
+    with pytest.raises(dna.DnaError):
+        dna.Dfa(np.array([[0, 0, 0, 2]], np.uint32), np.array([0], np.uint8))
+    big = dna.Dfa.from_kmers(synth.random_kmers(1, 400, 12))
+    with pytest.raises(dna.DnaError) as ei:
+        dna.scan(big, seq, plan=dict(placement=1))
+    assert ei.value.code == -3
+
+
+# ------------------------------------------------------ full-size workloads
+
+def test_plain_markov_full_size_launch_config():
+    """256 MiB order-2 Markov, ACG[AT]{2,6}C(G|T)T, count + positions, automatic plan
+    (the launch configuration the bench times)."""
+    seq, pat = synth.plain_markov()
+    c = check("regex", pat, seq)
+    assert c > 1000
+
+
+def test_plain_large_full_size_count():
+    """3.2 GiB with soft-masked and N runs, AC of 1,000 random 12-mers, count only."""
+    seq, kmers = synth.plain_large()
+    t, a = oracle.compile_kmers(kmers, minimise=True)
+    want_c, _ = oracle.run(t, a, seq, positions=False)
+    dfa = dna.Dfa.from_kmers(kmers)
+    dseq = torch.from_numpy(seq).cuda()
+    del seq
+    c, _ = gpu_run(dfa, dseq, positions=False)
+    assert c == want_c

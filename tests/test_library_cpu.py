@@ -1,0 +1,121 @@
+"""CPU-only checks of the library: it loads without a GPU, exports every symbol the
+header declares, its host compiler agrees with the oracle's independent compiler, and
+its automaton analysis agrees with brute force."""
+import ctypes
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1509_01506_gb300 as dna
+import synth
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "dna_dfa.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_loads_and_exports_header_symbols():
+    lib = ctypes.CDLL(dna.build())
+    names = header_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(dna.EXPORTED) <= set(names)
+
+
+def test_status_strings():
+    for code in range(-8, 1):
+        assert dna.status_string(code) not in ("", "unknown status")
+    assert dna.status_string(-99) == "unknown status"
+
+
+def _oracle_accept(mask, n):
+    return np.unpackbits(mask, bitorder="little")[:n]
+
+
+PATTERNS = [
+    "TATAAA", "ACG[AT]{2,6}C(G|T)T", "A(C|G)*T", "(AC)+G", "A.{2}T", "[AG]C?T", "G{2,}A",
+    "(A|CG|TTA)T", "T(A|C){1,3}(G|T)", "AAA", "A[CG]*T[AT]?G", "|".join(synth.REGEX_DNA_TABLE_V),
+] + synth.random_regexes(3, 40)
+
+
+@pytest.mark.parametrize("pattern", PATTERNS)
+def test_host_compiler_matches_oracle_compiler(pattern):
+    """Library (Glushkov + Hopcroft) and oracle (Thompson + Moore) minimal DFAs, both in
+    canonical breadth-first numbering, must be identical tables."""
+    t, m = dna.compile_regex(pattern)
+    to, ao = oracle.compile_regex(pattern)
+    assert t.shape == to.shape
+    assert (t == to).all()
+    assert (_oracle_accept(m, t.shape[0]) == ao).all()
+
+
+def test_kmer_compiler_matches_oracle():
+    for seed in range(20):
+        kmers = synth.random_kmers(seed, 1 + seed * 3, 4, 12)
+        t, m = dna.compile_kmers(kmers)
+        to, ao = oracle.compile_kmers(kmers, minimise=True)
+        assert (t == to).all() and (_oracle_accept(m, t.shape[0]) == ao).all()
+
+
+@pytest.mark.parametrize("bad,code", [("A|", -6), ("(AC", -6), ("[AX]", -6), ("A{3,1}", -6),
+                                      ("A*", -7), ("(AC)?", -7), ("", -6), ("A{0}", -6)])
+def test_compiler_errors(bad, code):
+    with pytest.raises(dna.DnaError) as ei:
+        dna.compile_regex(bad)
+    assert ei.value.code == code
+
+
+def brute_definite_depth(table, cap=10):
+    """Smallest m <= cap such that every word of length m maps all states to one."""
+    Q = table.shape[0]
+    sets = [frozenset(range(Q))]
+    for m in range(0, cap + 1):
+        if all(len(s) == 1 for s in sets):
+            return m
+        nxt = set()
+        for s in sets:
+            for c in range(4):
+                nxt.add(frozenset(int(table[q, c]) for q in s))
+        sets = list(nxt)
+    return -1
+
+
+def test_definite_depth_against_brute_force():
+    rng = np.random.default_rng(4)
+    tables = [dna.compile_regex(p)[0] for p in PATTERNS[:11]]
+    for _ in range(60):  # random small tables (many are not definite)
+        Q = int(rng.integers(1, 7))
+        t = rng.integers(0, Q, size=(Q, 4)).astype(np.uint32)
+        tables.append(t)
+    for t in tables:
+        got = dna.definite_depth(t)
+        want = brute_definite_depth(t, cap=10)
+        if want >= 0:
+            assert got == want
+        else:
+            assert got == -1 or got > 10
+
+
+def test_definite_depth_closed_form_for_kmers():
+    """An Aho-Corasick automaton of k-mers is k-definite (its state is the longest
+    suffix of the input that is a pattern prefix, a function of the last k symbols)."""
+    for k in (3, 6, 9):
+        t, _ = dna.compile_kmers(synth.random_kmers(k, 30, k))
+        assert dna.definite_depth(t) == k
+
+
+def test_pack_accept_layout():
+    a = np.zeros(19, dtype=np.uint8)
+    a[[0, 9, 18]] = 1
+    m = dna.pack_accept(a)
+    assert m.tolist() == [1, 2, 4]
