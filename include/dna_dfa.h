@@ -135,12 +135,15 @@ int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t 
  *   warps_per_cta  4, 8 or 16; 0 = automatic.
  *   placement      DNA_PLACE_*; 0 = automatic. A placement the automaton does not fit
  *                  in returns DNA_ERR_CAPACITY.
+ *   prefetch_tiles how many 128-byte tiles ahead each lane prefetches its chunk into L2;
+ *                  0 = automatic, 255 = no prefetch, at most 64 otherwise.
  */
 typedef struct {
     uint32_t chunk_bytes;
     uint32_t lookback;
     uint32_t warps_per_cta;
     uint32_t placement;
+    uint32_t prefetch_tiles;
 } dna_plan;
 
 int dna_scan_planned(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,

@@ -43,7 +43,8 @@ class _Info(ctypes.Structure):
 
 class _Plan(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint32), ("lookback", ctypes.c_uint32),
-                ("warps_per_cta", ctypes.c_uint32), ("placement", ctypes.c_uint32)]
+                ("warps_per_cta", ctypes.c_uint32), ("placement", ctypes.c_uint32),
+                ("prefetch_tiles", ctypes.c_uint32)]
 
 
 class _Profile(ctypes.Structure):
@@ -252,7 +253,8 @@ def scan(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None,
     L = lib()
     if plan:
         pl = _Plan(plan.get("chunk_bytes", 0), plan.get("lookback", 0),
-                   plan.get("warps_per_cta", 0), plan.get("placement", 0))
+                   plan.get("warps_per_cta", 0), plan.get("placement", 0),
+                   plan.get("prefetch_tiles", 0))
         rc = L.dna_scan_planned(dfa.handle, seq.data_ptr(), seq.numel(), sh,
                                 out_count.data_ptr(), pos_ptr, cap, ctypes.byref(pl))
     else:

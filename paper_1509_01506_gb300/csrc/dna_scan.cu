@@ -49,13 +49,14 @@ namespace {
 // ------------------------------------------------------------------ constants
 
 constexpr int kTile = 128;          // bytes per chunk row staged per step
-constexpr int kStages = 2;          // cp.async pipeline depth
+constexpr int kStages = 1;          // one stage per warp: rows are copied to registers first
 constexpr int kStageBytes = 32 * kTile;
-constexpr int kStashCap = 16;       // positions kept per chunk before a rescan
+constexpr int kStashCap = 8;        // hit-row records kept per chunk before a rescan
 constexpr int kPairRowBytes = 16 * 32 * 4;  // 16 symbol pairs x 32 lanes x 4 bytes
 constexpr uint32_t kMaxLookback = 64;
 constexpr int kResolveThreads = 256;
 constexpr uint32_t kMaxStates = 1u << 24;
+constexpr uint32_t kDefaultPrefetch = 0;  // tiles of L2 prefetch ahead of the stage
 
 enum Mode { MODE_PAIR = 0, MODE_ONE_SMEM = 1, MODE_ONE_GLOBAL = 2 };
 
@@ -87,6 +88,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
                  :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+template <int OFF>
+__device__ __forceinline__ void cp_async16_full(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0+%2], [%1], 16;\n"
+                 :: "r"(dst), "l"(src), "n"(OFF) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" :: "n"(N) : "memory"); }
@@ -115,175 +121,363 @@ struct ScanParams {
     uint32_t *spec_start;   // [nseg] speculated start state
     uint32_t *last_state;   // [nseg] state after the chunk (from the speculated start)
     uint32_t *count;        // [nseg] accepting steps (from the speculated start)
-    uint32_t *stash;        // [nseg][kStashCap] chunk-relative positions, or null
+    uint32_t *stash;        // [nseg][kStashCap][3] hit rows {tile, start state, count before}, or null
+    uint32_t prefetch_tiles; // L2 prefetch distance in tiles (0 = off)
+    uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
+    // 1, 2^16, 2^5, 2^28 passed at run time so the compiler keeps the multiplies that
+    // use them (adds and shifts) on the FMA pipe instead of turning them into ALU ops
+    uint32_t k1, k16, k5, k28;
+    // lowercase letters selected by the codes (a, c at bytes 0, 2; t, g at bytes 4, 6),
+    // passed at run time so that they stay in registers across the unrolled row loop
+    uint32_t lut_lo, lut_hi;
 };
 
-// Per-byte walk over bytes [k0, k1) of the lane's staged 128-byte row; 16-byte chunk c
-// of the row is stored at slot c ^ (lane & 7).
-template <bool kStash>
-__device__ __forceinline__ uint32_t row_bytes_swz(const OneTable &T, uint32_t q, const uint8_t *srow,
-                                                  int lane, int k0, int k1, uint32_t &cnt,
-                                                  uint32_t row_rel, uint32_t *stash) {
-    for (int k = k0; k < k1; ++k) {
-        uint32_t byte = srow[(((k >> 4) ^ (lane & 7)) << 4) | (k & 15)];
-        uint32_t e = T.step(q, byte);
+// Per-byte walk over a full 128-byte row held in registers (rows with reset bytes).
+__device__ __forceinline__ uint32_t row_bytes_reg(const OneTable &T, uint32_t q, const uint32_t (&w)[32],
+                                                  uint32_t &cnt) {
+#pragma unroll
+    for (int k = 0; k < kTile; ++k) {
+        uint32_t e = T.step(q, (w[k >> 2] >> (8 * (k & 3))) & 0xFFu);
         q = e & 0x7FFFFFFFu;
-        if (e >> 31) {
-            if (kStash && cnt < (uint32_t)kStashCap) stash[cnt] = row_rel + (uint32_t)k;
-            ++cnt;
-        }
+        cnt += e >> 31;
     }
     return q;
 }
 
-template <int MODE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
+// Per-byte walk over aligned offsets [from, to) read from global memory (the first row
+// of an unaligned sequence and the last row of the last chunk).
+__device__ __forceinline__ uint32_t row_bytes_global(const OneTable &T, uint32_t q, const uint8_t *abase,
+                                                     uint64_t from, uint64_t to, uint32_t &cnt) {
+    for (uint64_t o = from; o < to; ++o) {
+        uint32_t e = T.step(q, abase[o]);
+        q = e & 0x7FFFFFFFu;
+        cnt += e >> 31;
+    }
+    return q;
+}
+
+// Records a row that contains accepting steps: the emit pass re-walks it from 'q_row'
+// and writes its positions starting at the chunk's offset + 'cnt_before'.
+__device__ __forceinline__ void record_hit_row(uint32_t *stash, uint32_t &nrec, uint32_t t,
+                                               uint32_t q_row, uint32_t cnt_before) {
+    if (nrec < (uint32_t)kStashCap) {
+        stash[nrec * 3] = t;
+        stash[nrec * 3 + 1] = q_row;
+        stash[nrec * 3 + 2] = cnt_before;
+    }
+    ++nrec;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
+}
+
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// Pair-table entry layout (lane l's copy): bits 0..17 = shared address of the next
+// state's row for lane l (row base 2048-aligned, so bits 7..10 are zero), bits 27..28 =
+// accepting steps in the pair. The two codes of a pair enter at bits 7..10.
+constexpr uint32_t kPairMuxMask = 0x78000780u;
+constexpr int kCountShift = 27;
+
+// Bitwise select with the pair-table mask: bits of b where kPairMuxMask is set, bits of a
+// elsewhere. Written as one lop3 (lut 0xD8 = (a & ~c) | (b & c)); the C++ form of the
+// same select compiles to two logic instructions.
+__device__ __forceinline__ uint32_t mux_pair(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xD8;" : "=r"(d) : "r"(a), "r"(b), "n"(kPairMuxMask));
+    return d;
+}
+
+// After a chunk's speculative run was repaired at its converging point (the true start
+// and the speculated start met within the chunk's first row), the hit-row records of the
+// speculative run are made those of the true run: row 0 is re-walked from the true start,
+// later rows keep their start states (the runs coincide there) and shift their count
+// offsets by delta = true prefix count - speculative prefix count. 'pa' is the true run's
+// count over the prefix; if the true prefix has accepting steps but row 0 had no record,
+// a record for row 0 is inserted in front.
+__device__ __forceinline__ void fix_hit_rows(uint32_t *stash, uint32_t &nrec, uint32_t q_true,
+                                             uint32_t delta, uint32_t pa) {
+    const uint32_t n = nrec < (uint32_t)kStashCap ? nrec : (uint32_t)kStashCap;
+    bool row0 = false;
+    for (uint32_t r = 0; r < n; ++r) {
+        if (stash[3 * r] == 0) { stash[3 * r + 1] = q_true; row0 = true; }
+        else stash[3 * r + 2] += delta;
+    }
+    if (!row0 && pa > 0) {
+        if (nrec < (uint32_t)kStashCap) {
+            for (uint32_t r = n; r > 0; --r) {
+                stash[3 * r] = stash[3 * (r - 1)];
+                stash[3 * r + 1] = stash[3 * (r - 1) + 1];
+                stash[3 * r + 2] = stash[3 * (r - 1) + 2];
+            }
+            stash[0] = 0; stash[1] = q_true; stash[2] = 0;
+        }
+        ++nrec;   // beyond the capacity: the extraction pass rescans the chunk
+    }
+}
+
+template <int MODE, int WARPS, bool POS>
+__global__ void __launch_bounds__(WARPS * 32, 1)
 scan_kernel(ScanParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint32_t warp_last[WARPS];
+    __shared__ uint4 head_s[WARPS * 32];   // each chunk's first 16 bytes, for the repair
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
 
-    // shared memory layout: [staging: WARPS*kStages*4 KB][one-symbol table][pad][pair table]
+    // shared memory: [staging: WARPS x 4 KB][one-symbol table][compact pair table][pad][pair table]
     uint8_t *stage_ptr = smem + (size_t)warp * kStages * kStageBytes;
     const uint32_t stage_addr = smem_base + (uint32_t)warp * kStages * kStageBytes;
     uint32_t *one_s = reinterpret_cast<uint32_t *>(smem + (size_t)WARPS * kStages * kStageBytes);
+
+    const uint64_t seg0 = ((uint64_t)blockIdx.x * WARPS + warp) * 32u;
+    const uint64_t seg = seg0 + lane;
+    const bool warp_busy = seg0 < p.nseg;
+    const bool active = seg < p.nseg;
+    const uint64_t S = p.seg_bytes;
+    const uint64_t b = seg * S;   // aligned offset of this chunk
+    const uint32_t ntiles = warp_busy ? (uint32_t)(S / kTile) : 0u;
+
+    // ---- staging: each warp copies tile t of its 32 chunks into a swizzled [32 rows][128 B]
+    // stage. Copy j (0..7) of a lane moves the 16-byte column lane & 7 of row 4j + lane/8,
+    // so each copy instruction of the warp covers four whole 128-byte lines. Only the warp
+    // holding the last chunk can run past the end of the sequence and checks bounds.
+    const uint32_t l8 = (uint32_t)lane >> 3, cc = (uint32_t)lane & 7u;
+    const uint64_t copy_off0 = (seg0 + l8) * S + cc * 16u;
+    const uint32_t copy_dst0 = stage_addr + l8 * kTile + ((cc ^ l8) << 4);
+    // odd copies land in rows with (row & 7) >= 4: their swizzled column differs in bit 2
+    const uint32_t copy_dst1 = stage_addr + l8 * kTile + ((cc ^ l8 ^ 4u) << 4);
+    const bool tail_warp = seg0 + 32 >= p.nseg;
+    const uint8_t *copy_src = p.abase + copy_off0;   // copy 0 of the next tile to issue
+    const uint64_t stride4 = 4u * S;                 // four chunk rows apart
+    auto issue = [&](uint32_t t) {
+        if (!tail_warp) {
+            // every row of this warp lies inside the sequence: no checks
+            const uint8_t *src = copy_src + (uint64_t)t * kTile;
+            cp_async16_full<0 * 4 * kTile>(copy_dst0, src);
+            cp_async16_full<1 * 4 * kTile>(copy_dst1, src + stride4);
+            cp_async16_full<2 * 4 * kTile>(copy_dst0, src + 2 * stride4);
+            cp_async16_full<3 * 4 * kTile>(copy_dst1, src + 3 * stride4);
+            cp_async16_full<4 * 4 * kTile>(copy_dst0, src + 4 * stride4);
+            cp_async16_full<5 * 4 * kTile>(copy_dst1, src + 5 * stride4);
+            cp_async16_full<6 * 4 * kTile>(copy_dst0, src + 6 * stride4);
+            cp_async16_full<7 * 4 * kTile>(copy_dst1, src + 7 * stride4);
+            return;
+        }
+        const uint64_t base = copy_off0 + (uint64_t)t * kTile;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint64_t goff = base + (uint64_t)j * stride4;
+            const bool ok = seg0 + 4u * j + l8 < p.nseg && goff < p.hi;
+            const uint32_t dst = ((j & 1) ? copy_dst1 : copy_dst0) + (uint32_t)j * 4u * kTile;
+            cp_async16(dst, ok ? p.abase + goff : p.abase, ok ? 16u : 0u);
+        }
+    };
+    auto prefetch = [&](uint32_t t) {   // this lane's own row of tile t into L2
+        uint64_t off = b + (uint64_t)t * kTile;
+        if (active && t < ntiles && off < p.hi) prefetch_l2(p.abase + off);
+    };
+    // the (small) compact tables are loaded first, so that these loads are not queued
+    // behind the first tile's copies
+    const uint32_t n1 = MODE == MODE_ONE_GLOBAL ? 0u : p.n_states * 4u;
+    const uint32_t nc = MODE == MODE_PAIR ? p.n_states * 16u : 0u;
+    constexpr int kPre = 2048 / (WARPS * 32) > 0 ? 2048 / (WARPS * 32) : 1;
+    uint32_t pre[kPre];
+#pragma unroll
+    for (int r = 0; r < kPre; ++r) {
+        const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
+        pre[r] = i < n1 ? p.one[i] : (i < n1 + nc ? p.pair[i - n1] : 0u);
+    }
+    if (ntiles) issue(0);
+    cp_async_commit();
+    for (uint32_t t = 1; t < 1 + p.prefetch_tiles; ++t) prefetch(t);
+    const bool has_lookback = active && b > p.lo && p.lookback > 0;
+
     OneTable T;
     T.reset_entry = p.reset_entry;
     uint32_t pair_base = 0;
     if (MODE == MODE_ONE_GLOBAL) {
         T.t = p.one;
     } else {
-        const uint32_t n1 = p.n_states * 4u;
-        for (uint32_t i = threadIdx.x; i < n1; i += WARPS * 32) one_s[i] = p.one[i];
+        // one-symbol table, then (pair mode) the compact pair table right after it
+        uint32_t *tabs = one_s;
+#pragma unroll
+        for (int r = 0; r < kPre; ++r) {
+            const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
+            if (i < n1 + nc) tabs[i] = pre[r];
+        }
+        for (uint32_t i = threadIdx.x + (uint32_t)kPre * WARPS * 32; i < n1 + nc; i += WARPS * 32)
+            tabs[i] = i < n1 ? p.one[i] : p.pair[i - n1];
         T.t = one_s;
         if (MODE == MODE_PAIR) {
-            uint32_t after_one = smem_base + (uint32_t)WARPS * kStages * kStageBytes + n1 * 4u;
-            pair_base = (after_one + 2047u) & ~2047u;   // bits 0..10 of the base are zero
+            // every lane's copy of the pair table is expanded from the compact copy
+            const uint32_t *cbuf = one_s + n1;
+            uint32_t after_c = smem_base + (uint32_t)WARPS * kStages * kStageBytes + (n1 + nc) * 4u;
+            pair_base = (after_c + 2047u) & ~2047u;   // bits 0..10 of the base are zero
+            uint32_t *pair_ptr = reinterpret_cast<uint32_t *>(smem + (pair_base - smem_base));
+            __syncthreads();
             const uint32_t n2 = p.n_states * 16u * 32u;
-            uint8_t *pair_ptr = smem + (pair_base - smem_base);
             for (uint32_t i = threadIdx.x; i < n2; i += WARPS * 32) {
-                uint32_t q = i >> 9, pr = (i >> 5) & 15u, l = i & 31u;
-                uint32_t e = p.pair[q * 16u + pr];
+                uint32_t e = cbuf[i >> 5];
                 uint32_t nx = e & 0x00FFFFFFu, c = e >> 24;
-                reinterpret_cast<uint32_t *>(pair_ptr)[i] =
-                    (c << 24) | (pair_base + nx * (uint32_t)kPairRowBytes + l * 4u);
-                (void)q;
+                pair_ptr[i] = (c << kCountShift) | (pair_base + nx * (uint32_t)kPairRowBytes + (i & 31u) * 4u);
             }
         }
     }
     __syncthreads();
+    uint32_t *stash = POS ? p.stash + seg * (kStashCap * 3) : nullptr;
+    uint32_t nrec = 0;
 
-    const uint64_t seg0 = ((uint64_t)blockIdx.x * WARPS + warp) * 32u;
-    if (seg0 >= p.nseg) return;   // whole warp idle (no block-wide sync follows)
-    const uint64_t seg = seg0 + lane;
-    const bool active = seg < p.nseg;
-    const uint64_t S = p.seg_bytes;
-    const uint64_t b = seg * S;   // aligned offset of this chunk
-    const uint32_t ntiles = (uint32_t)(S / kTile);
-    uint32_t *stash = p.stash ? p.stash + seg * kStashCap : nullptr;
-
-    // ---- speculation: run from q0 over the lookback window in front of the chunk
+    // ---- speculated start state: q0, or the state reached from q0 over the lookback window
     uint32_t q = 0;
-    if (active && b > p.lo) {
-        uint64_t from = b - p.lo > p.lookback ? b - p.lookback : p.lo;
+    if (has_lookback) {   // the 'lookback' bytes in front of the chunk
+        const uint64_t from = b - p.lo > p.lookback ? b - p.lookback : p.lo;
         for (uint64_t off = from; off < b; ++off) q = T.step(q, p.abase[off]) & 0x7FFFFFFFu;
     }
-    const uint32_t spec = q;
+    uint32_t spec = q;
     uint32_t cnt = 0;
     uint32_t cur = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
 
-    // ---- staging pipeline prologue
-    auto issue = [&](uint32_t t) {
-        const uint32_t st = t % kStages;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            int f = j * 32 + lane;
-            int r = f >> 3, c = f & 7;
-            uint64_t rseg = seg0 + r;
-            uint64_t goff = rseg * S + (uint64_t)t * kTile + (uint64_t)c * 16u;
-            bool ok = rseg < p.nseg && goff < p.hi;
-            const uint8_t *src = ok ? p.abase + goff : p.abase;
-            uint32_t dst = stage_addr + st * kStageBytes + r * kTile + ((c ^ (r & 7)) * 16);
-            cp_async16(dst, src, ok ? 16u : 0u);
-        }
-    };
-#pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) {
-        if ((uint32_t)s < ntiles) issue(s);
-        cp_async_commit();
+    // tiles [t_full0, t_full1) of this chunk lie entirely inside the sequence; tiles from
+    // t_live on lie past its end (only the last chunk has any)
+    uint32_t t_live = 0, t_full0 = 0, t_full1 = 0;
+    if (active) {
+        const uint64_t rem = p.hi - b;
+        t_live = rem >= S ? ntiles : (uint32_t)((rem + kTile - 1) / kTile);
+        t_full1 = rem >= S ? ntiles : (uint32_t)(rem / kTile);
+        t_full0 = b < p.lo ? 1u : 0u;
     }
-
+    const uint32_t lut_lo = p.lut_lo, lut_hi = p.lut_hi;
     for (uint32_t t = 0; t < ntiles; ++t) {
-        __syncwarp();   // every lane is done with the stage the next issue overwrites
-        if (t + kStages - 1 < ntiles) issue(t + kStages - 1);
-        cp_async_commit();
-        cp_async_wait<kStages - 1>();
+        cp_async_wait<0>();
         __syncwarp();   // tile t of all 32 rows is visible to the warp
-        if (!active) continue;
         const uint64_t row_off = b + (uint64_t)t * kTile;
-        if (row_off >= p.hi) continue;   // past the end of the sequence (last chunk)
-        // the lane's row, un-swizzled: 16-byte chunk c sits at slot c ^ (lane & 7)
-        const uint8_t *srow = stage_ptr + (t % kStages) * kStageBytes + lane * kTile;
-        const uint32_t row_rel = (uint32_t)(t * kTile);
-        const bool full = row_off >= p.lo && row_off + kTile <= p.hi;
-        const int k0 = row_off < p.lo ? (int)(p.lo - row_off) : 0;
-        const int k1 = row_off + kTile > p.hi ? (int)(p.hi - row_off) : kTile;
+        const bool live = t < t_live;
+        const bool full = t >= t_full0 && t < t_full1;
+        uint32_t w[32];
+        {
+            // the lane's row, un-swizzled: 16-byte chunk c sits at slot c ^ (lane & 7)
+            const uint8_t *srow = stage_ptr + lane * kTile;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                uint4 v = *reinterpret_cast<const uint4 *>(srow + ((c ^ (lane & 7)) * 16));
+                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+            }
+        }
+        __syncwarp();   // every lane holds its row: the stage can be refilled
+        if (t + 1 < ntiles) issue(t + 1);
+        cp_async_commit();
+        if (p.prefetch_tiles) prefetch(t + 1 + p.prefetch_tiles);
+        if (t == 0) head_s[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+        if (!live) continue;
 
         if (MODE == MODE_PAIR) {
             bool done = false;
             if (full) {
-                uint32_t w[32];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    uint4 v = *reinterpret_cast<const uint4 *>(srow + ((c ^ (lane & 7)) * 16));
-                    w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
-                }
-                uint32_t acc = 0, err = 0, c2 = cur;
+                uint32_t acc = 0, err = 0, rc = 0, c2 = cur;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
-                    uint32_t x = w[k] & 0x06060606u;
-                    uint32_t y = x * 65u;
-                    uint32_t e1 = lds_u32((c2 & 0x00FFFFFFu) | (y & 0x780u));
-                    uint32_t e2 = lds_u32((e1 & 0x00FFFFFFu) | ((y >> 16) & 0x780u));
-                    acc += e1 + e2;
+                    // codes of the 4 bytes sit at bits 1..2 of each byte of x; y = x*65
+                    // puts the first pair at bits 7..10 and the second at bits 23..26, and
+                    // is zero at bits 27..30, so the mux below forms clean addresses
+                    const uint32_t x = w[k] & 0x06060606u;
+                    const uint32_t y = mad_lo(x, 65u, 0u);
+                    const uint32_t e1 = lds_u32(mux_pair(c2, y));
+                    const uint32_t e2 = lds_u32(mux_pair(e1, y >> 16));
+                    acc = mad_lo(e1, p.k1, acc);
+                    acc = mad_lo(e2, p.k1, acc);
                     c2 = e2;
-                    // bit-exact base check: expected lowercase word from the codes
-                    uint32_t z = x | (x >> 4);
-                    uint32_t sel = __byte_perm(z, 0, 0x0020);
-                    uint32_t expect = __byte_perm(0x00630061u, 0x00670074u, sel);
+                    if (k % 3 == 2 || k == 31) {     // <= 6 entries: count <= 12 fits bits 27..30
+                        rc = mad_hi(acc, p.k5, rc);  // rc += acc >> 27
+                        acc = 0;
+                    }
+                    // bit-exact base check: expected lowercase bytes selected by the codes
+                    const uint32_t z = x | (x >> 4);
+                    const uint32_t sel = __byte_perm(z, 0, 0x0020);
+                    const uint32_t expect = __byte_perm(lut_lo, lut_hi, sel);
                     err |= expect ^ w[k];
                 }
                 if ((err & 0xDFDFDFDFu) == 0) {
-                    uint32_t rc = acc >> 24;
-                    if (stash && rc) {
-                        uint32_t qs = ((cur & 0x00FFFFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-                        row_bytes_swz<true>(T, qs, srow, lane, 0, kTile, cnt, row_rel, stash);
-                    } else {
-                        cnt += rc;
-                    }
-                    cur = c2 & 0x00FFFFFFu;
+                    if (POS && rc)
+                        record_hit_row(stash, nrec, t,
+                                       ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes, cnt);
+                    cnt += rc;
+                    cur = c2 & 0x3FFFFu;
                     done = true;
                 }
             }
             if (!done) {
-                uint32_t qs = ((cur & 0x00FFFFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-                if (stash) qs = row_bytes_swz<true>(T, qs, srow, lane, k0, k1, cnt, row_rel, stash);
-                else qs = row_bytes_swz<false>(T, qs, srow, lane, k0, k1, cnt, row_rel, nullptr);
-                cur = pair_base + qs * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
+                uint32_t qs = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+                uint32_t before = cnt;
+                // a reset byte or a sequence edge in this row: walk it from global memory
+                // (the row was just staged, so it is in L2)
+                uint32_t qe = row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
+                                               row_off + kTile < p.hi ? row_off + kTile : p.hi, cnt);
+                if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
+                cur = pair_base + qe * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
             }
         } else {
-            if (stash) q = row_bytes_swz<true>(T, q, srow, lane, k0, k1, cnt, row_rel, stash);
-            else q = row_bytes_swz<false>(T, q, srow, lane, k0, k1, cnt, row_rel, nullptr);
+            uint32_t before = cnt, qs = q;
+            q = full ? row_bytes_reg(T, qs, w, cnt)
+                     : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
+                                        row_off + kTile < p.hi ? row_off + kTile : p.hi, cnt);
+            if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
         }
     }
     cp_async_wait<0>();
-    if (!active) return;
     uint32_t last = q;
-    if (MODE == MODE_PAIR) last = ((cur & 0x00FFFFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+    if (MODE == MODE_PAIR) last = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+
+    // ---- join inside the block (Sec. III-A) with repair at the converging point (Alg. 1):
+    // the true start of a chunk is the last state of the chunk before it, which the lane
+    // to the left (or, for lane 0, the previous warp's lane 31) has just computed
+    if (lane == 31) warp_last[warp] = last;
+    __syncthreads();
+    uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, last, 1);
+    if (lane == 0) prev = warp > 0 ? warp_last[warp - 1] : 0u;
+    const bool has_prev = active && seg > 0 && (lane > 0 || warp > 0);
+    if (has_prev && prev != spec) {
+        // run the true start and the speculated start in lockstep over the chunk's first
+        // bytes; at the first step where their states are equal, the rest of the chunk is
+        // identical for both runs
+        const uint64_t vlen64 = p.hi - b;
+        const uint32_t vlen = vlen64 < 16 ? (uint32_t)vlen64 : 16u;
+        const uint4 h4 = head_s[threadIdx.x];   // the chunk's first 16 bytes
+        const uint32_t head[4] = {h4.x, h4.y, h4.z, h4.w};
+        uint32_t qa = prev, qs = spec, pa = 0, ps = 0;
+        bool conv = false;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (!conv && (uint32_t)k < vlen) {
+                const uint32_t byte = (head[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+                const uint32_t ea = T.step(qa, byte), es = T.step(qs, byte);
+                qa = ea & 0x7FFFFFFFu; qs = es & 0x7FFFFFFFu;
+                pa += ea >> 31; ps += es >> 31;
+                conv = qa == qs;
+            }
+        }
+        if (conv) {
+            const uint32_t delta = pa - ps;   // modulo 2^32; the corrected count is exact
+            cnt += delta;
+            if (POS) fix_hit_rows(stash, nrec, prev, delta, pa);
+            spec = prev;
+        }
+    }
+    if (!active) return;
     p.spec_start[seg] = spec;
     p.last_state[seg] = last;
     p.count[seg] = cnt;
+    if (POS) p.nrec[seg] = nrec;
 }
 
 // ------------------------------------------------------------ resolve kernels
@@ -295,11 +489,12 @@ struct ResolveParams {
     uint32_t reset_entry;
     const uint32_t *spec_start, *last_state, *count;
     uint32_t *true_start, *true_last, *true_count;
-    uint8_t *flags;             // bit0 corrected, bit1 never met, bit2 last state differs
+    uint8_t *flags;             // bit0: rescan for positions, bit1 never met, bit2 last state differs
     unsigned long long *block_sum;  // [nblocks]
     uint32_t *div_list;         // chunks whose true last state differs
     uint32_t *div_count;
     uint32_t div_cap;
+    uint32_t *stash, *nrec;     // hit-row records (positions requested) or null
 };
 
 __device__ __forceinline__ uint32_t one_step(const uint32_t *one, uint32_t reset_entry, uint32_t q,
@@ -308,7 +503,10 @@ __device__ __forceinline__ uint32_t one_step(const uint32_t *one, uint32_t reset
 }
 
 // Converging-point repair (Sec. III-B.3, Alg. 1): run the true start 'a' and the
-// speculated start 's' in lockstep over chunk c until their states meet.
+// speculated start 's' in lockstep over chunk c until their states meet; from there on
+// the speculative results hold, so count(a) = own prefix count + speculative total -
+// speculative prefix count. If the runs meet inside the chunk's first row the hit-row
+// records are fixed for extraction; otherwise the chunk is marked for a rescan.
 __device__ void repair_chunk(const ResolveParams &p, uint64_t c, uint32_t a, uint32_t s,
                              uint32_t spec_total, uint32_t spec_last,
                              uint32_t &out_count, uint32_t &out_last, uint8_t &out_flags) {
@@ -325,7 +523,16 @@ __device__ void repair_chunk(const ResolveParams &p, uint64_t c, uint32_t a, uin
         if (qa == qs) {   // converging point: the rest of the runs coincide
             out_count = ca + (spec_total - cs);
             out_last = spec_last;
-            out_flags = 1;
+            out_flags = 0;
+            if (p.stash) {
+                if (off < b + kTile) {
+                    uint32_t nr = p.nrec[c];
+                    fix_hit_rows(p.stash + c * (kStashCap * 3), nr, a, ca - cs, ca);
+                    p.nrec[c] = nr;
+                } else {
+                    out_flags = 1;
+                }
+            }
             return;
         }
     }
@@ -384,6 +591,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ResolveParams p, uint64_
                 if (a != p.true_start[c]) {
                     uint32_t cnt, last; uint8_t fl;
                     repair_chunk(p, c, a, p.spec_start[c], p.count[c], p.last_state[c], cnt, last, fl);
+                    fl |= 1;
                     long long d = (long long)cnt - (long long)p.true_count[c];
                     p.block_sum[c / kResolveThreads] += (unsigned long long)d;
                     p.true_start[c] = a; p.true_count[c] = cnt; p.true_last[c] = last;
@@ -409,10 +617,11 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ResolveParams p, uint64_
                     uint32_t a = cur_last;
                     if (a == p.spec_start[k]) { cnt = p.count[k]; last = p.last_state[k]; }
                     else repair_chunk(p, k, a, p.spec_start[k], p.count[k], p.last_state[k], cnt, last, fl);
+                    fl |= 1;
                     long long d = (long long)cnt - (long long)p.true_count[k];
                     p.block_sum[k / kResolveThreads] += (unsigned long long)d;
                     p.true_start[k] = a; p.true_count[k] = cnt; p.true_last[k] = last;
-                    p.flags[k] = fl | 1;
+                    p.flags[k] = fl;
                     cur_last = last;
                     ++k;
                 }
@@ -456,12 +665,23 @@ struct EmitParams {
     uint64_t lo, hi, seg_bytes, nseg;
     const uint32_t *one;
     uint32_t reset_entry;
-    const uint32_t *true_start, *true_count, *stash;
+    const uint32_t *true_start, *true_count, *stash, *nrec;
     const uint8_t *flags;
     const unsigned long long *block_off;
     uint64_t *out;
     uint64_t cap;
 };
+
+// Walks aligned offsets [from, to) from state q, writing each accepting step's sequence
+// position to out[off], off+1, ... (stops at the capacity).
+__device__ void emit_walk(const EmitParams &p, uint64_t from, uint64_t to, uint32_t q,
+                          unsigned long long off) {
+    for (uint64_t o = from; o < to && off < p.cap; ++o) {
+        uint32_t e = one_step(p.one, p.reset_entry, q, p.abase[o]);
+        q = e & 0x7FFFFFFFu;
+        if (e >> 31) p.out[off++] = o - p.lo;
+    }
+}
 
 __global__ void __launch_bounds__(kResolveThreads) emit_kernel(EmitParams p) {
     __shared__ unsigned long long wsum[kResolveThreads / 32];
@@ -480,21 +700,21 @@ __global__ void __launch_bounds__(kResolveThreads) emit_kernel(EmitParams p) {
     unsigned long long off = p.block_off[blockIdx.x] + before + x - v;
     if (off >= p.cap || v == 0) return;
     const uint64_t b = c * p.seg_bytes;
-    if (p.flags[c] == 0 && v <= (unsigned long long)kStashCap) {
-        for (uint32_t k = 0; k < (uint32_t)v && off + k < p.cap; ++k)
-            p.out[off + k] = b + p.stash[c * kStashCap + k] - p.lo;
+    const uint64_t cend = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
+    const uint32_t nr = p.nrec[c];
+    if (p.flags[c] == 0 && nr <= (uint32_t)kStashCap) {
+        // the speculated run was the true run: re-walk only the rows that had matches
+        const uint32_t *rec = p.stash + c * (kStashCap * 3);
+        for (uint32_t r = 0; r < nr; ++r) {
+            uint64_t rs = b + (uint64_t)rec[3 * r] * kTile;
+            uint64_t from = rs > p.lo ? rs : p.lo;
+            uint64_t to = rs + kTile < cend ? rs + kTile : cend;
+            emit_walk(p, from, to, rec[3 * r + 1], off + rec[3 * r + 2]);
+        }
         return;
     }
-    // rescan from the true start
-    uint64_t from = b > p.lo ? b : p.lo;
-    uint64_t to = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
-    uint32_t q = p.true_start[c];
-    uint64_t k = 0;
-    for (uint64_t o = from; o < to && off + k < p.cap; ++o) {
-        uint32_t e = one_step(p.one, p.reset_entry, q, p.abase[o]);
-        q = e & 0x7FFFFFFFu;
-        if (e >> 31) { p.out[off + k] = o - p.lo; ++k; }
-    }
+    // corrected or overflowing chunk: rescan it from its true start
+    emit_walk(p, b > p.lo ? b : p.lo, cend, p.true_start[c], off);
 }
 
 __global__ void write_zero_kernel(uint64_t *out) { *out = 0; }
@@ -535,21 +755,30 @@ DeviceProps device_props(int dev) {
     return cache[dev];
 }
 
+// Dynamic shared memory of the scan kernel (the launch argument).
 size_t scan_smem_bytes(int mode, int warps, uint32_t n_states) {
     size_t s = (size_t)warps * kStages * kStageBytes;
     if (mode == MODE_ONE_GLOBAL) return s;
     s += (size_t)n_states * 16;
-    if (mode == MODE_PAIR) s += 2048 + (size_t)n_states * kPairRowBytes;
+    if (mode == MODE_PAIR) s += (size_t)n_states * 64 + 2048 + (size_t)n_states * kPairRowBytes;
     return s;
+}
+
+// Static shared memory of the scan kernel: each chunk's first 16 bytes + one word per warp.
+size_t scan_static_smem(int warps) { return (size_t)warps * 32 * 16 + (size_t)warps * 4; }
+
+size_t scan_total_smem(int mode, int warps, uint32_t n_states) {
+    return scan_smem_bytes(mode, warps, n_states) + scan_static_smem(warps);
 }
 
 using ScanFn = void (*)(ScanParams);
 
-ScanFn scan_fn(int mode, int warps) {
-#define PICK(M, W) if (mode == M && warps == W) return scan_kernel<M, W>;
-    PICK(MODE_PAIR, 4) PICK(MODE_PAIR, 8) PICK(MODE_PAIR, 16)
-    PICK(MODE_ONE_SMEM, 4) PICK(MODE_ONE_SMEM, 8) PICK(MODE_ONE_SMEM, 16)
-    PICK(MODE_ONE_GLOBAL, 4) PICK(MODE_ONE_GLOBAL, 8) PICK(MODE_ONE_GLOBAL, 16)
+ScanFn scan_fn(int mode, int warps, bool pos) {
+#define PICK(M, W)                                                   \
+    if (mode == M && warps == W) return pos ? scan_kernel<M, W, true> : scan_kernel<M, W, false>;
+    PICK(MODE_PAIR, 8) PICK(MODE_PAIR, 16) PICK(MODE_PAIR, 24) PICK(MODE_PAIR, 32)
+    PICK(MODE_ONE_SMEM, 8) PICK(MODE_ONE_SMEM, 16) PICK(MODE_ONE_SMEM, 24) PICK(MODE_ONE_SMEM, 32)
+    PICK(MODE_ONE_GLOBAL, 8) PICK(MODE_ONE_GLOBAL, 16) PICK(MODE_ONE_GLOBAL, 24) PICK(MODE_ONE_GLOBAL, 32)
 #undef PICK
     return nullptr;
 }
@@ -574,41 +803,46 @@ namespace {
 constexpr int kColOfCode[4] = {0, 1, 3, 2};
 
 size_t max_pair_states(size_t smem_optin, int warps) {
-    size_t fixed = (size_t)warps * kStages * kStageBytes + 2048;
+    size_t fixed = (size_t)warps * kStages * kStageBytes + 2048 + scan_static_smem(warps);
     if (smem_optin <= fixed) return 0;
-    return (smem_optin - fixed) / (kPairRowBytes + 16);
+    return (smem_optin - fixed) / (kPairRowBytes + 16 + 64);
 }
 
 struct Plan {
     int mode, warps;
+    bool pos;
+    uint32_t prefetch;
     uint64_t seg_bytes, nseg;
     uint32_t lookback;
     size_t smem;
     int grid;
 };
 
-int make_plan(const dna_dfa *d, uint64_t total, const dna_plan *ov, Plan &pl) {
+int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Plan &pl) {
     DeviceProps pr = device_props(d->device);
     const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
     int mode;
     uint32_t req = ov ? ov->placement : 0;
     int warps = ov && ov->warps_per_cta ? (int)ov->warps_per_cta : 0;
-    if (warps && warps != 4 && warps != 8 && warps != 16) return DNA_ERR_INVALID_ARG;
+    if (warps && warps != 8 && warps != 16 && warps != 24 && warps != 32) return DNA_ERR_INVALID_ARG;
     if (req == DNA_PLACE_AUTO) req = d->placement;
     if (req == DNA_PLACE_SMEM_PAIR) mode = MODE_PAIR;
     else if (req == DNA_PLACE_SMEM_ONE) mode = MODE_ONE_SMEM;
     else if (req == DNA_PLACE_GLOBAL_ONE) mode = MODE_ONE_GLOBAL;
     else return DNA_ERR_INVALID_ARG;
     if (!warps) {
-        warps = 4;
-        for (int w : {16, 8}) if (scan_smem_bytes(mode, w, d->n_states) <= optin) { warps = w; break; }
+        warps = 8;
+        for (int w : {24, 16}) if (scan_total_smem(mode, w, d->n_states) <= optin) { warps = w; break; }
     }
     size_t smem = scan_smem_bytes(mode, warps, d->n_states);
-    if (smem > optin) return DNA_ERR_CAPACITY;
+    if (scan_total_smem(mode, warps, d->n_states) > optin) return DNA_ERR_CAPACITY;
     uint32_t lb = ov && ov->lookback ? ov->lookback : d->lookback;
     if (lb > kMaxLookback) return DNA_ERR_INVALID_ARG;
-    ScanFn fn = scan_fn(mode, warps);
+    ScanFn fn = scan_fn(mode, warps, pos);
     if (!fn) return DNA_ERR_INVALID_ARG;
+    uint32_t pf = kDefaultPrefetch;
+    if (ov && ov->prefetch_tiles) pf = ov->prefetch_tiles >= 255 ? 0 : ov->prefetch_tiles;
+    if (pf > 64) return DNA_ERR_INVALID_ARG;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     int per_sm = 1;
@@ -624,7 +858,7 @@ int make_plan(const dna_dfa *d, uint64_t total, const dna_plan *ov, Plan &pl) {
         S = (S + kTile - 1) / kTile * kTile;
         if (S < kTile) S = kTile;
     }
-    pl.mode = mode; pl.warps = warps; pl.seg_bytes = S;
+    pl.mode = mode; pl.warps = warps; pl.seg_bytes = S; pl.pos = pos; pl.prefetch = pf;
     pl.nseg = (total + S - 1) / S;
     pl.lookback = lb; pl.smem = smem;
     uint64_t lanes_per_cta = (uint64_t)warps * 32;
@@ -635,7 +869,7 @@ int make_plan(const dna_dfa *d, uint64_t total, const dna_plan *ov, Plan &pl) {
 // device scratch carved from one stream-ordered allocation
 struct Scratch {
     uint32_t *spec_start, *last_state, *count, *true_start, *true_last, *true_count, *stash;
-    uint32_t *div_list, *div_count;
+    uint32_t *div_list, *div_count, *nrec;
     uint8_t *flags;
     unsigned long long *block_sum, *block_off;
     void *base;
@@ -658,7 +892,8 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
     s.div_count = (uint32_t *)take(4);
     s.div_list = (uint32_t *)take((size_t)div_cap * 4);
     s.flags = (uint8_t *)take(nseg);
-    s.stash = positions ? (uint32_t *)take(nseg * kStashCap * 4) : nullptr;
+    s.stash = positions ? (uint32_t *)take(nseg * kStashCap * 12) : nullptr;
+    s.nrec = positions ? (uint32_t *)take(nseg * 4) : nullptr;
     s.bytes = off;
     s.base = base;
 }
@@ -680,10 +915,10 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;
     const uint64_t total = len + shift;
-    Plan pl;
-    int rc = make_plan(d, total, ov, pl);
-    if (rc) return rc;
     const bool positions = out_positions != nullptr && cap > 0;
+    Plan pl;
+    int rc = make_plan(d, total, positions, ov, pl);
+    if (rc) return rc;
     const uint64_t nblocks = (pl.nseg + kResolveThreads - 1) / kResolveThreads;
     const uint32_t div_cap = 4096;
     Scratch s;
@@ -699,6 +934,10 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     sp.one = d->d_one; sp.pair = d->d_pair;
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
     sp.stash = s.stash;
+    sp.prefetch_tiles = pl.prefetch;
+    sp.nrec = s.nrec;
+    sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
+    sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = g_profile.load(std::memory_order_relaxed) != 0;
@@ -708,7 +947,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         cudaEventRecord(ev0, stream);
     }
     if (e == cudaSuccess) {
-        scan_fn(pl.mode, pl.warps)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);
+        scan_fn(pl.mode, pl.warps, pl.pos)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);
         e = cudaGetLastError();
         record_launch();
     }
@@ -724,6 +963,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     rp.true_start = s.true_start; rp.true_last = s.true_last; rp.true_count = s.true_count;
     rp.flags = s.flags; rp.block_sum = s.block_sum;
     rp.div_list = s.div_list; rp.div_count = s.div_count; rp.div_cap = div_cap;
+    rp.stash = s.stash; rp.nrec = s.nrec;
     if (e == cudaSuccess) {
         resolve_kernel<<<(unsigned)nblocks, kResolveThreads, 0, stream>>>(rp);
         e = cudaGetLastError();
@@ -739,6 +979,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         ep.abase = abase; ep.lo = shift; ep.hi = total; ep.seg_bytes = pl.seg_bytes; ep.nseg = pl.nseg;
         ep.one = d->d_one; ep.reset_entry = d->reset_entry;
         ep.true_start = s.true_start; ep.true_count = s.true_count; ep.stash = s.stash;
+        ep.nrec = s.nrec;
         ep.flags = s.flags; ep.block_off = s.block_off; ep.out = out_positions; ep.cap = cap;
         emit_kernel<<<(unsigned)nblocks, kResolveThreads, 0, stream>>>(ep);
         e = cudaGetLastError();
@@ -778,16 +1019,18 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
             one[4ull * q + c] = nx | (acc(nx) << 31);
         }
     d->definite_depth = dnalib::definite_depth(table, n_states, (int)kMaxLookback, 4096);
-    if (d->definite_depth >= 0) d->lookback = (uint32_t)d->definite_depth;
-    else d->lookback = 32;
+    // q0 speculation repaired from the chunk's first 16 bytes works whenever runs meet
+    // within 16 symbols (definite depth <= 16, and in practice most automata on DNA);
+    // a known larger depth gets an exact lookback instead
+    d->lookback = (d->definite_depth > 16) ? (uint32_t)d->definite_depth : 0u;
     DeviceProps pr = device_props(dev);
     size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
-    if (n_states <= max_pair_states(optin, 4)) d->placement = DNA_PLACE_SMEM_PAIR;
-    else if (scan_smem_bytes(MODE_ONE_SMEM, 4, n_states) <= optin) d->placement = DNA_PLACE_SMEM_ONE;
+    if (n_states <= max_pair_states(optin, 8)) d->placement = DNA_PLACE_SMEM_PAIR;
+    else if (scan_total_smem(MODE_ONE_SMEM, 8, n_states) <= optin) d->placement = DNA_PLACE_SMEM_ONE;
     else d->placement = DNA_PLACE_GLOBAL_ONE;
     cudaError_t e = cudaMalloc(&d->d_one, sizeof(uint32_t) * one.size());
     if (e == cudaSuccess) e = cudaMemcpy(d->d_one, one.data(), sizeof(uint32_t) * one.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && n_states <= max_pair_states(optin, 4)) {
+    if (e == cudaSuccess && n_states <= max_pair_states(optin, 8)) {
         std::vector<uint32_t> pair(16ull * n_states);
         for (uint32_t q = 0; q < n_states; ++q)
             for (int b0 = 0; b0 < 4; ++b0)

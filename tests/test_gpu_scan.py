@@ -113,12 +113,12 @@ def test_random_motif_regexes(pattern):
 # ------------------------------------------------------ plan independence
 
 PLANS = [
-    dict(chunk_bytes=128, lookback=1, warps_per_cta=4, placement=1),
+    dict(chunk_bytes=128, lookback=1, warps_per_cta=32, placement=1),
     dict(chunk_bytes=256, lookback=3, warps_per_cta=8, placement=1),
     dict(chunk_bytes=1152, lookback=12, warps_per_cta=16, placement=1),
     dict(chunk_bytes=8192, lookback=32, warps_per_cta=16, placement=1),
     dict(chunk_bytes=384, lookback=1, warps_per_cta=8, placement=2),
-    dict(chunk_bytes=640, lookback=5, warps_per_cta=4, placement=3),
+    dict(chunk_bytes=640, lookback=5, warps_per_cta=32, placement=3),
     dict(chunk_bytes=4096, lookback=64, warps_per_cta=16, placement=2),
 ]
 
