@@ -54,7 +54,6 @@ constexpr int kStageBytes = 32 * kTile;
 constexpr int kStashCap = 8;        // hit-row records kept per chunk before a rescan
 constexpr int kPairRowBytes = 16 * 32 * 4;  // 16 symbol pairs x 32 lanes x 4 bytes
 constexpr uint32_t kMaxLookback = 64;
-constexpr int kResolveThreads = 256;
 constexpr uint32_t kMaxStates = 1u << 24;
 constexpr uint32_t kDefaultPrefetch = 0;  // tiles of L2 prefetch ahead of the stage
 
@@ -124,6 +123,16 @@ struct ScanParams {
     uint32_t *stash;        // [nseg][kStashCap][3] hit rows {tile, start state, count before}, or null
     uint32_t prefetch_tiles; // L2 prefetch distance in tiles (0 = off)
     uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
+    uint8_t *flags;         // [nseg] 1 = extraction must rescan the chunk from its true start
+    uint32_t *ctrl;         // [4] zeroed before launch: finish ticket, pending, diverged, 0
+    uint32_t *pending;      // chunks the last block must repair (first chunk of each block,
+    uint32_t pending_cap;   //   and chunks whose 16-byte repair did not converge)
+    uint32_t *pending_a;    // [pending_cap] snapshot of each pending chunk's true start
+    uint32_t *div_list;     // [div_cap] chunks whose last state changed in a repair
+    uint32_t div_cap;
+    unsigned long long *cta_sum;   // [grid] count of each block's chunks
+    unsigned long long *cta_off;   // [grid] exclusive prefix of cta_sum (for extraction)
+    uint64_t *out_count;
     // 1, 2^16, 2^5, 2^28 passed at run time so the compiler keeps the multiplies that
     // use them (adds and shifts) on the FMA pipe instead of turning them into ALU ops
     uint32_t k1, k16, k5, k28;
@@ -138,18 +147,6 @@ __device__ __forceinline__ uint32_t row_bytes_reg(const OneTable &T, uint32_t q,
 #pragma unroll
     for (int k = 0; k < kTile; ++k) {
         uint32_t e = T.step(q, (w[k >> 2] >> (8 * (k & 3))) & 0xFFu);
-        q = e & 0x7FFFFFFFu;
-        cnt += e >> 31;
-    }
-    return q;
-}
-
-// Per-byte walk over aligned offsets [from, to) read from global memory (the first row
-// of an unaligned sequence and the last row of the last chunk).
-__device__ __forceinline__ uint32_t row_bytes_global(const OneTable &T, uint32_t q, const uint8_t *abase,
-                                                     uint64_t from, uint64_t to, uint32_t &cnt) {
-    for (uint64_t o = from; o < to; ++o) {
-        uint32_t e = T.step(q, abase[o]);
         q = e & 0x7FFFFFFFu;
         cnt += e >> 31;
     }
@@ -225,6 +222,210 @@ __device__ __forceinline__ void fix_hit_rows(uint32_t *stash, uint32_t &nrec, ui
     }
 }
 
+__device__ __forceinline__ uint32_t one_step(const uint32_t *one, uint32_t reset_entry, uint32_t q,
+                                             uint32_t b) {
+    return byte_is_base(b) ? one[q * 4u + ((b >> 1) & 3u)] : reset_entry;
+}
+
+// Walks aligned offsets [from, to) of the sequence in 128-byte blocks: each block is
+// fetched with eight independent 16-byte loads (a 16-byte granule is loaded only if it
+// starts before 'hi', so no load leaves the sequence's last page), then f(offset, byte)
+// is called in order. f returns false to stop the walk.
+template <class F>
+__device__ __forceinline__ void walk_range(const uint8_t *abase, uint64_t from, uint64_t to, uint64_t hi,
+                                           F &&f) {
+    for (uint64_t blk = from & ~(uint64_t)(kTile - 1); blk < to; blk += kTile) {
+        uint4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint64_t g = blk + 16u * j;
+            v[j] = g < hi ? *reinterpret_cast<const uint4 *>(abase + g) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int k4 = 0; k4 < 32; ++k4) {
+            const uint4 &vv = v[k4 >> 2];
+            const uint32_t word = (k4 & 3) == 0 ? vv.x : (k4 & 3) == 1 ? vv.y : (k4 & 3) == 2 ? vv.z : vv.w;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint64_t o = blk + 4u * k4 + i;
+                if (o >= from && o < to && !f(o, (word >> (8 * i)) & 0xFFu)) return;
+            }
+        }
+    }
+}
+
+// Per-byte walk over aligned offsets [from, to) read from global memory: rows with a
+// reset byte, the first row of an unaligned sequence and the last row of the last chunk.
+__device__ __forceinline__ uint32_t row_bytes_global(const OneTable &T, uint32_t q, const uint8_t *abase,
+                                                     uint64_t from, uint64_t to, uint64_t hi, uint32_t &cnt) {
+    walk_range(abase, from, to, hi, [&](uint64_t, uint32_t byte) {
+        const uint32_t e = T.step(q, byte);
+        q = e & 0x7FFFFFFFu;
+        cnt += e >> 31;
+        return true;
+    });
+    return q;
+}
+
+// Converging-point repair (Sec. III-B.3, Alg. 1) of chunk c from global memory: the true
+// start 'a' and the start 's' that the chunk's current results assume run in lockstep
+// until their states meet; from there on both runs coincide, so the true count is the
+// true prefix count + (current count - assumed prefix count) and the last state is
+// unchanged. A run that never meets gives the chunk's true count and last state directly.
+// Hit-row records are fixed when the runs meet inside row 0; otherwise the chunk is
+// flagged for a rescan by the extraction pass. Requires the chunk's current results
+// (count, last state, records) to be those of the run from 's'.
+struct Repair { uint32_t count, last; uint8_t flag; };
+
+__device__ Repair repair_chunk(const ScanParams &p, uint64_t c, uint32_t a, uint32_t s) {
+    const uint64_t b = c * p.seg_bytes;
+    const uint64_t from = b > p.lo ? b : p.lo;
+    const uint64_t to = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
+    uint32_t qa = a, qs = s, ca = 0, cs = 0;
+    uint64_t met_at = ~0ull;
+    walk_range(p.abase, from, to, p.hi, [&](uint64_t off, uint32_t byte) {
+        const uint32_t ea = one_step(p.one, p.reset_entry, qa, byte);
+        const uint32_t es = one_step(p.one, p.reset_entry, qs, byte);
+        qa = ea & 0x7FFFFFFFu; qs = es & 0x7FFFFFFFu;
+        ca += ea >> 31; cs += es >> 31;
+        if (qa == qs) { met_at = off; return false; }
+        return true;
+    });
+    Repair r;
+    if (met_at != ~0ull) {
+        r.count = p.count[c] - cs + ca;
+        r.last = p.last_state[c];
+        r.flag = 0;
+        if (p.stash) {
+            if (met_at < b + kTile) {
+                uint32_t nr = p.nrec[c];
+                fix_hit_rows(p.stash + c * (kStashCap * 3), nr, a, ca - cs, ca);
+                p.nrec[c] = nr;
+            } else {
+                r.flag = 1;
+            }
+        }
+    } else {
+        r.count = ca;
+        r.last = qa;
+        r.flag = 1;
+    }
+    return r;
+}
+
+// Makes chunk c's results those of the run from its true start a: count (and its block
+// sum), assumed start, last state, flags.
+__device__ __forceinline__ void apply_repair(const ScanParams &p, uint64_t c, uint32_t a,
+                                             const Repair &r, uint32_t chunks_per_block) {
+    const uint32_t old = p.count[c];
+    p.count[c] = r.count;
+    atomicAdd(&p.cta_sum[c / chunks_per_block], (unsigned long long)(long long)((int64_t)r.count - (int64_t)old));
+    p.spec_start[c] = a;
+    p.last_state[c] = r.last;
+    if (r.flag) p.flags[c] = 1;
+}
+
+// The join across blocks (Sec. III-A "binary reduction"), run by the last block to
+// finish: repairs the pending chunks in parallel (each from the last state of the chunk
+// before it, as it stood when the blocks finished), then walks forward from every chunk
+// whose last state changed until the chain agrees again, then writes the total count and
+// each block's output offset. Every chunk's (assumed start, count, last state) triple
+// stays consistent throughout.
+template <int THREADS>
+__device__ void finalize_block(const ScanParams &p) {
+    __shared__ unsigned long long wsum[THREADS / 32];
+    __shared__ unsigned long long carry;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t cpb = THREADS;   // chunks per scan block
+    const uint32_t np = p.ctrl[1];
+    if (np <= p.pending_cap) {
+        for (uint32_t i = tid; i < np; i += THREADS) p.pending_a[i] = p.last_state[p.pending[i] - 1];
+        __syncthreads();
+        for (uint32_t i = tid; i < np; i += THREADS) {
+            const uint64_t c = p.pending[i];
+            const uint32_t a = p.pending_a[i];
+            const uint32_t s = p.spec_start[c];
+            if (a == s) continue;
+            const uint32_t old_last = p.last_state[c];
+            const Repair r = repair_chunk(p, c, a, s);
+            apply_repair(p, c, a, r, cpb);
+            if (r.last != old_last) {
+                const uint32_t k = atomicAdd(&p.ctrl[2], 1u);
+                if (k < p.div_cap) p.div_list[k] = (uint32_t)c;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t nd = p.ctrl[2];
+        if (np > p.pending_cap || nd > p.div_cap) {
+            // a list overflowed: check every chunk boundary in order
+            for (uint64_t c = 1; c < p.nseg; ++c) {
+                const uint32_t a = p.last_state[c - 1];
+                const uint32_t s = p.spec_start[c];
+                if (a == s) continue;
+                const Repair r = repair_chunk(p, c, a, s);
+                apply_repair(p, c, a, r, cpb);
+            }
+        } else if (nd > 0) {
+            // sort the (small) list of chunks whose last state changed, then walk forward
+            for (uint32_t i = 1; i < nd; ++i) {
+                const uint32_t vc = p.div_list[i];
+                uint32_t j = i;
+                while (j > 0 && p.div_list[j - 1] > vc) { p.div_list[j] = p.div_list[j - 1]; --j; }
+                p.div_list[j] = vc;
+            }
+            uint64_t walked = 0;
+            for (uint32_t i = 0; i < nd; ++i) {
+                const uint64_t c = p.div_list[i];
+                if (c < walked) continue;   // already recomputed from its true start
+                // the walk stops exactly where the next chunk's assumed start is the true
+                // last state of the chunk before it
+                uint32_t cur = p.last_state[c];
+                uint64_t k = c + 1;
+                for (;;) {
+                    if (k >= p.nseg || cur == p.spec_start[k]) { walked = k; break; }
+                    const Repair r = repair_chunk(p, k, cur, p.spec_start[k]);
+                    apply_repair(p, k, cur, r, cpb);
+                    p.flags[k] = 1;   // its records follow a start that was not the true one
+                    cur = r.last;
+                    ++k;
+                }
+            }
+        }
+        carry = 0;
+    }
+    __syncthreads();
+    // exclusive scan of the block sums -> output offsets; total -> out_count
+    const uint32_t nb = gridDim.x;
+    for (uint32_t base = 0; base < nb; base += THREADS) {
+        const uint32_t i = base + tid;
+        const unsigned long long v = i < nb ? p.cta_sum[i] : 0ull;
+        unsigned long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if ((tid & 31) >= (uint32_t)o) x += y;
+        }
+        if ((tid & 31) == 31) wsum[tid >> 5] = x;
+        __syncthreads();
+        if (tid < 32) {
+            unsigned long long t = tid < THREADS / 32 ? wsum[tid] : 0ull;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+                if (tid >= (uint32_t)o) t += y;
+            }
+            if (tid < THREADS / 32) wsum[tid] = t;
+        }
+        __syncthreads();
+        const unsigned long long incl = x + ((tid >> 5) ? wsum[(tid >> 5) - 1] : 0ull) + carry;
+        if (i < nb) p.cta_off[i] = incl - v;
+        __syncthreads();
+        if (tid == THREADS - 1) carry = incl;
+        __syncthreads();
+    }
+    if (tid == 0) *p.out_count = carry;
+}
+
 template <int MODE, int WARPS, bool POS>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 scan_kernel(ScanParams p) {
@@ -289,14 +490,16 @@ scan_kernel(ScanParams p) {
     };
     // the (small) compact tables are loaded first, so that these loads are not queued
     // behind the first tile's copies
-    const uint32_t n1 = MODE == MODE_ONE_GLOBAL ? 0u : p.n_states * 4u;
+    const uint32_t n1 = p.n_states * 4u;
     const uint32_t nc = MODE == MODE_PAIR ? p.n_states * 16u : 0u;
     constexpr int kPre = 2048 / (WARPS * 32) > 0 ? 2048 / (WARPS * 32) : 1;
     uint32_t pre[kPre];
+    if constexpr (MODE != MODE_ONE_GLOBAL) {
 #pragma unroll
-    for (int r = 0; r < kPre; ++r) {
-        const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
-        pre[r] = i < n1 ? p.one[i] : (i < n1 + nc ? p.pair[i - n1] : 0u);
+        for (int r = 0; r < kPre; ++r) {
+            const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
+            pre[r] = i < n1 ? p.one[i] : (i < n1 + nc ? p.pair[i - n1] : 0u);
+        }
     }
     if (ntiles) issue(0);
     cp_async_commit();
@@ -306,7 +509,7 @@ scan_kernel(ScanParams p) {
     OneTable T;
     T.reset_entry = p.reset_entry;
     uint32_t pair_base = 0;
-    if (MODE == MODE_ONE_GLOBAL) {
+    if constexpr (MODE == MODE_ONE_GLOBAL) {
         T.t = p.one;
     } else {
         // one-symbol table, then (pair mode) the compact pair table right after it
@@ -422,7 +625,7 @@ scan_kernel(ScanParams p) {
                 // a reset byte or a sequence edge in this row: walk it from global memory
                 // (the row was just staged, so it is in L2)
                 uint32_t qe = row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
-                                               row_off + kTile < p.hi ? row_off + kTile : p.hi, cnt);
+                                               row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
                 if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
                 cur = pair_base + qe * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
             }
@@ -430,7 +633,7 @@ scan_kernel(ScanParams p) {
             uint32_t before = cnt, qs = q;
             q = full ? row_bytes_reg(T, qs, w, cnt)
                      : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
-                                        row_off + kTile < p.hi ? row_off + kTile : p.hi, cnt);
+                                        row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
             if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
         }
     }
@@ -446,6 +649,7 @@ scan_kernel(ScanParams p) {
     uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, last, 1);
     if (lane == 0) prev = warp > 0 ? warp_last[warp - 1] : 0u;
     const bool has_prev = active && seg > 0 && (lane > 0 || warp > 0);
+    bool pending = active && seg > 0 && !has_prev;   // first chunk of the block
     if (has_prev && prev != spec) {
         // run the true start and the speculated start in lockstep over the chunk's first
         // bytes; at the first step where their states are equal, the rest of the chunk is
@@ -471,250 +675,130 @@ scan_kernel(ScanParams p) {
             cnt += delta;
             if (POS) fix_hit_rows(stash, nrec, prev, delta, pa);
             spec = prev;
+        } else {
+            pending = true;   // the last block repairs it from global memory
         }
     }
-    if (!active) return;
-    p.spec_start[seg] = spec;
-    p.last_state[seg] = last;
-    p.count[seg] = cnt;
-    if (POS) p.nrec[seg] = nrec;
-}
-
-// ------------------------------------------------------------ resolve kernels
-
-struct ResolveParams {
-    const uint8_t *abase;
-    uint64_t lo, hi, seg_bytes, nseg;
-    const uint32_t *one;        // global one-symbol table
-    uint32_t reset_entry;
-    const uint32_t *spec_start, *last_state, *count;
-    uint32_t *true_start, *true_last, *true_count;
-    uint8_t *flags;             // bit0: rescan for positions, bit1 never met, bit2 last state differs
-    unsigned long long *block_sum;  // [nblocks]
-    uint32_t *div_list;         // chunks whose true last state differs
-    uint32_t *div_count;
-    uint32_t div_cap;
-    uint32_t *stash, *nrec;     // hit-row records (positions requested) or null
-};
-
-__device__ __forceinline__ uint32_t one_step(const uint32_t *one, uint32_t reset_entry, uint32_t q,
-                                             uint32_t b) {
-    return byte_is_base(b) ? one[q * 4u + ((b >> 1) & 3u)] : reset_entry;
-}
-
-// Converging-point repair (Sec. III-B.3, Alg. 1): run the true start 'a' and the
-// speculated start 's' in lockstep over chunk c until their states meet; from there on
-// the speculative results hold, so count(a) = own prefix count + speculative total -
-// speculative prefix count. If the runs meet inside the chunk's first row the hit-row
-// records are fixed for extraction; otherwise the chunk is marked for a rescan.
-__device__ void repair_chunk(const ResolveParams &p, uint64_t c, uint32_t a, uint32_t s,
-                             uint32_t spec_total, uint32_t spec_last,
-                             uint32_t &out_count, uint32_t &out_last, uint8_t &out_flags) {
-    uint64_t b = c * p.seg_bytes;
-    uint64_t from = b > p.lo ? b : p.lo;
-    uint64_t to = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
-    uint32_t qa = a, qs = s, ca = 0, cs = 0;
-    for (uint64_t off = from; off < to; ++off) {
-        uint32_t byte = p.abase[off];
-        uint32_t ea = one_step(p.one, p.reset_entry, qa, byte);
-        uint32_t es = one_step(p.one, p.reset_entry, qs, byte);
-        qa = ea & 0x7FFFFFFFu; qs = es & 0x7FFFFFFFu;
-        ca += ea >> 31; cs += es >> 31;
-        if (qa == qs) {   // converging point: the rest of the runs coincide
-            out_count = ca + (spec_total - cs);
-            out_last = spec_last;
-            out_flags = 0;
-            if (p.stash) {
-                if (off < b + kTile) {
-                    uint32_t nr = p.nrec[c];
-                    fix_hit_rows(p.stash + c * (kStashCap * 3), nr, a, ca - cs, ca);
-                    p.nrec[c] = nr;
-                } else {
-                    out_flags = 1;
-                }
-            }
-            return;
-        }
+    if (active) {
+        p.spec_start[seg] = spec;
+        p.last_state[seg] = last;
+        p.count[seg] = cnt;
+        p.flags[seg] = 0;
+        if (POS) p.nrec[seg] = nrec;
     }
-    out_count = ca;
-    out_last = qa;
-    out_flags = (uint8_t)(1 | 2 | (qa != spec_last ? 4 : 0));
-}
-
-__global__ void __launch_bounds__(kResolveThreads) resolve_kernel(ResolveParams p) {
-    __shared__ unsigned long long red[kResolveThreads / 32];
-    const uint64_t c = (uint64_t)blockIdx.x * kResolveThreads + threadIdx.x;
-    uint32_t tc = 0;
-    if (c < p.nseg) {
-        uint32_t a = c == 0 ? 0u : p.last_state[c - 1];
-        uint32_t s = p.spec_start[c];
-        uint32_t cnt = p.count[c], last = p.last_state[c];
-        uint8_t fl = 0;
-        if (a != s) {
-            repair_chunk(p, c, a, s, cnt, last, cnt, last, fl);
-            if (fl & 4) {
-                uint32_t k = atomicAdd(p.div_count, 1u);
-                if (k < p.div_cap) p.div_list[k] = (uint32_t)c;
-            }
-        }
-        p.true_start[c] = a;
-        p.true_last[c] = last;
-        p.true_count[c] = cnt;
-        p.flags[c] = fl;
-        tc = cnt;
+    if (pending) {
+        const uint32_t k = atomicAdd(&p.ctrl[1], 1u);
+        if (k < p.pending_cap) p.pending[k] = (uint32_t)seg;
     }
-    unsigned long long v = tc;
+    __threadfence();   // this thread's results are visible before the block's ticket
+    // block sum of the chunk counts
+    unsigned long long v = active ? cnt : 0u;
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __shared__ unsigned long long red[WARPS];
+    __shared__ int is_last;
+    if (lane == 0) red[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long s = 0;
-        for (int i = 0; i < kResolveThreads / 32; ++i) s += red[i];
-        p.block_sum[blockIdx.x] = s;
+        unsigned long long t = 0;
+        for (int i = 0; i < WARPS; ++i) t += red[i];
+        p.cta_sum[blockIdx.x] = t;
+        __threadfence();
+        is_last = atomicAdd(&p.ctrl[0], 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    finalize_block<WARPS * 32>(p);
 }
 
-// Sequential cascade over chunks whose true last state differs from the speculated
-// one, then the exclusive scan of block sums and the total count. One block.
-__global__ void __launch_bounds__(1024) finalize_kernel(ResolveParams p, uint64_t nblocks,
-                                                        unsigned long long *block_off,
-                                                        uint64_t *out_count) {
-    __shared__ unsigned long long carry;
-    __shared__ unsigned long long wsum[32];
-    if (threadIdx.x == 0) {
-        uint32_t nd = *p.div_count;
-        if (nd > p.div_cap) {
-            // list overflowed: walk every chunk sequentially from the start
-            uint32_t prev_last = 0;
-            for (uint64_t c = 0; c < p.nseg; ++c) {
-                uint32_t a = c == 0 ? 0u : prev_last;
-                if (a != p.true_start[c]) {
-                    uint32_t cnt, last; uint8_t fl;
-                    repair_chunk(p, c, a, p.spec_start[c], p.count[c], p.last_state[c], cnt, last, fl);
-                    fl |= 1;
-                    long long d = (long long)cnt - (long long)p.true_count[c];
-                    p.block_sum[c / kResolveThreads] += (unsigned long long)d;
-                    p.true_start[c] = a; p.true_count[c] = cnt; p.true_last[c] = last;
-                    p.flags[c] = fl;
-                }
-                prev_last = p.true_last[c];
-            }
-        } else if (nd > 0) {
-            // sort the (small) list, then walk forward from each entry until the chain agrees
-            for (uint32_t i = 1; i < nd; ++i) {
-                uint32_t v = p.div_list[i], j = i;
-                while (j > 0 && p.div_list[j - 1] > v) { p.div_list[j] = p.div_list[j - 1]; --j; }
-                p.div_list[j] = v;
-            }
-            uint64_t walked = 0;
-            for (uint32_t i = 0; i < nd; ++i) {
-                uint64_t c = p.div_list[i];
-                if (c < walked) continue;
-                uint32_t cur_last = p.true_last[c];
-                uint64_t k = c + 1;
-                while (k < p.nseg && cur_last != p.last_state[k - 1]) {
-                    uint32_t cnt, last; uint8_t fl = 0;
-                    uint32_t a = cur_last;
-                    if (a == p.spec_start[k]) { cnt = p.count[k]; last = p.last_state[k]; }
-                    else repair_chunk(p, k, a, p.spec_start[k], p.count[k], p.last_state[k], cnt, last, fl);
-                    fl |= 1;
-                    long long d = (long long)cnt - (long long)p.true_count[k];
-                    p.block_sum[k / kResolveThreads] += (unsigned long long)d;
-                    p.true_start[k] = a; p.true_count[k] = cnt; p.true_last[k] = last;
-                    p.flags[k] = fl;
-                    cur_last = last;
-                    ++k;
-                }
-                walked = k;
-            }
-        }
-        carry = 0;
-    }
-    __syncthreads();
-    // exclusive scan of block sums, 1024 at a time
-    for (uint64_t base = 0; base < nblocks; base += 1024) {
-        uint64_t i = base + threadIdx.x;
-        unsigned long long v = i < nblocks ? p.block_sum[i] : 0ull;
-        unsigned long long x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if ((threadIdx.x & 31) >= o) x += y;
-        }
-        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            unsigned long long s = wsum[threadIdx.x];
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, s, o);
-                if (threadIdx.x >= o) s += y;
-            }
-            wsum[threadIdx.x] = s;
-        }
-        __syncthreads();
-        unsigned long long incl = x + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0ull) + carry;
-        if (i < nblocks) block_off[i] = incl - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out_count = carry;
-}
+// ------------------------------------------------------------ extraction
 
 struct EmitParams {
     const uint8_t *abase;
     uint64_t lo, hi, seg_bytes, nseg;
     const uint32_t *one;
-    uint32_t reset_entry;
-    const uint32_t *true_start, *true_count, *stash, *nrec;
+    uint32_t reset_entry, n_states;
+    const uint32_t *last_state, *count, *stash, *nrec;
     const uint8_t *flags;
-    const unsigned long long *block_off;
+    const unsigned long long *cta_off;
     uint64_t *out;
     uint64_t cap;
 };
 
-// Walks aligned offsets [from, to) from state q, writing each accepting step's sequence
-// position to out[off], off+1, ... (stops at the capacity).
-__device__ void emit_walk(const EmitParams &p, uint64_t from, uint64_t to, uint32_t q,
-                          unsigned long long off) {
-    for (uint64_t o = from; o < to && off < p.cap; ++o) {
-        uint32_t e = one_step(p.one, p.reset_entry, q, p.abase[o]);
-        q = e & 0x7FFFFFFFu;
-        if (e >> 31) p.out[off++] = o - p.lo;
+// One block per scan block (same chunks). Each chunk's output offset is its block's
+// offset plus the block-exclusive prefix of the chunk counts. Recorded hit rows are
+// spread over all threads of the block; each is re-walked from its recorded start state
+// and its accepting positions written in order. Flagged or overflowing chunks are
+// rescanned from their true start (the previous chunk's last state).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) emit_kernel(EmitParams p) {
+    __shared__ unsigned long long s_off[THREADS];
+    __shared__ uint32_t s_slot[THREADS + 1];
+    __shared__ unsigned long long wsum[THREADS / 32];
+    __shared__ uint32_t wsum2[THREADS / 32];
+    extern __shared__ uint32_t one_s[];
+    const uint32_t tid = threadIdx.x;
+    const uint64_t c = (uint64_t)blockIdx.x * THREADS + tid;
+    const bool act = c < p.nseg;
+    const uint32_t *one = p.one;
+    if (p.n_states * 4u <= 8192u) {   // small tables (<= 32 KB): copy to shared memory
+        for (uint32_t i = tid; i < p.n_states * 4u; i += THREADS) one_s[i] = p.one[i];
+        one = one_s;
     }
-}
-
-__global__ void __launch_bounds__(kResolveThreads) emit_kernel(EmitParams p) {
-    __shared__ unsigned long long wsum[kResolveThreads / 32];
-    const uint64_t c = (uint64_t)blockIdx.x * kResolveThreads + threadIdx.x;
-    unsigned long long v = c < p.nseg ? p.true_count[c] : 0u;
+    const unsigned long long v = act ? p.count[c] : 0u;
+    const uint32_t nr = act ? p.nrec[c] : 0u;
+    const bool rescan = act && v > 0 && (p.flags[c] != 0 || nr > (uint32_t)kStashCap);
+    const uint32_t rows = (act && !rescan) ? nr : 0u;
+    // block-exclusive scans of counts and of hit rows
     unsigned long long x = v;
+    uint32_t y = rows;
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if ((threadIdx.x & 31) >= o) x += y;
+        const unsigned long long xa = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        const uint32_t ya = __shfl_up_sync(0xFFFFFFFFu, y, o);
+        if ((tid & 31) >= (uint32_t)o) { x += xa; y += ya; }
     }
-    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    if ((tid & 31) == 31) { wsum[tid >> 5] = x; wsum2[tid >> 5] = y; }
     __syncthreads();
-    unsigned long long before = 0;
-    for (int i = 0; i < (int)(threadIdx.x >> 5); ++i) before += wsum[i];
-    if (c >= p.nseg) return;
-    unsigned long long off = p.block_off[blockIdx.x] + before + x - v;
-    if (off >= p.cap || v == 0) return;
-    const uint64_t b = c * p.seg_bytes;
-    const uint64_t cend = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
-    const uint32_t nr = p.nrec[c];
-    if (p.flags[c] == 0 && nr <= (uint32_t)kStashCap) {
-        // the speculated run was the true run: re-walk only the rows that had matches
-        const uint32_t *rec = p.stash + c * (kStashCap * 3);
-        for (uint32_t r = 0; r < nr; ++r) {
-            uint64_t rs = b + (uint64_t)rec[3 * r] * kTile;
-            uint64_t from = rs > p.lo ? rs : p.lo;
-            uint64_t to = rs + kTile < cend ? rs + kTile : cend;
-            emit_walk(p, from, to, rec[3 * r + 1], off + rec[3 * r + 2]);
-        }
-        return;
+    unsigned long long bx = 0;
+    uint32_t by = 0;
+    for (uint32_t i = 0; i < (tid >> 5); ++i) { bx += wsum[i]; by += wsum2[i]; }
+    const unsigned long long off = p.cta_off[blockIdx.x] + bx + x - v;
+    s_off[tid] = off;
+    s_slot[tid] = by + y - rows;
+    if (tid == THREADS - 1) s_slot[THREADS] = by + y;
+    __syncthreads();
+    const uint32_t total_rows = s_slot[THREADS];
+
+    auto walk = [&](uint64_t from, uint64_t to, uint32_t q, unsigned long long o) {
+        walk_range(p.abase, from, to, p.hi, [&](uint64_t a, uint32_t byte) {
+            const uint32_t e = one_step(one, p.reset_entry, q, byte);
+            q = e & 0x7FFFFFFFu;
+            if (e >> 31) p.out[o++] = a - p.lo;
+            return o < p.cap;
+        });
+    };
+    const uint64_t S = p.seg_bytes;
+    if (rescan && off < p.cap) {
+        const uint64_t b = c * S;
+        walk(b > p.lo ? b : p.lo, b + S < p.hi ? b + S : p.hi, c ? p.last_state[c - 1] : 0u, off);
     }
-    // corrected or overflowing chunk: rescan it from its true start
-    emit_walk(p, b > p.lo ? b : p.lo, cend, p.true_start[c], off);
+    for (uint32_t r = tid; r < total_rows; r += THREADS) {
+        // the chunk owning hit-row slot r: largest j with s_slot[j] <= r
+        uint32_t lo = 0, hi = THREADS - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (s_slot[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t j = lo;
+        const uint64_t cj = (uint64_t)blockIdx.x * THREADS + j;
+        const uint32_t *rec = p.stash + cj * (kStashCap * 3) + 3 * (r - s_slot[j]);
+        const unsigned long long o = s_off[j] + rec[2];
+        if (o >= p.cap) continue;
+        const uint64_t b = cj * S;
+        const uint64_t cend = b + S < p.hi ? b + S : p.hi;
+        const uint64_t rs = b + (uint64_t)rec[0] * kTile;
+        walk(rs > p.lo ? rs : p.lo, rs + kTile < cend ? rs + kTile : cend, rec[1], o);
+    }
 }
 
 __global__ void write_zero_kernel(uint64_t *out) { *out = 0; }
@@ -765,7 +849,7 @@ size_t scan_smem_bytes(int mode, int warps, uint32_t n_states) {
 }
 
 // Static shared memory of the scan kernel: each chunk's first 16 bytes + one word per warp.
-size_t scan_static_smem(int warps) { return (size_t)warps * 32 * 16 + (size_t)warps * 4; }
+size_t scan_static_smem(int warps) { return (size_t)warps * 32 * 16 + (size_t)warps * 20 + 1024; }
 
 size_t scan_total_smem(int mode, int warps, uint32_t n_states) {
     return scan_smem_bytes(mode, warps, n_states) + scan_static_smem(warps);
@@ -868,37 +952,45 @@ int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Pl
 
 // device scratch carved from one stream-ordered allocation
 struct Scratch {
-    uint32_t *spec_start, *last_state, *count, *true_start, *true_last, *true_count, *stash;
-    uint32_t *div_list, *div_count, *nrec;
+    uint32_t *spec_start, *last_state, *count, *nrec, *stash, *pending, *pending_a, *div_list, *ctrl;
     uint8_t *flags;
-    unsigned long long *block_sum, *block_off;
-    void *base;
+    unsigned long long *cta_sum, *cta_off;
     size_t bytes;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t div_cap, uint8_t *base) {
+void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t pending_cap,
+           uint32_t div_cap, uint8_t *base) {
     size_t off = 0;
-    auto take = [&](size_t bytes) { uint8_t *p = base ? base + off : nullptr; off = align_up(off + bytes, 256); return p; };
-    s.block_sum = (unsigned long long *)take(nblocks * 8);
-    s.block_off = (unsigned long long *)take(nblocks * 8);
+    auto take = [&](size_t bytes) { uint8_t *q = base ? base + off : nullptr; off = align_up(off + bytes, 256); return q; };
+    s.ctrl = (uint32_t *)take(16);
+    s.cta_sum = (unsigned long long *)take(nblocks * 8);
+    s.cta_off = (unsigned long long *)take(nblocks * 8);
     s.spec_start = (uint32_t *)take(nseg * 4);
     s.last_state = (uint32_t *)take(nseg * 4);
     s.count = (uint32_t *)take(nseg * 4);
-    s.true_start = (uint32_t *)take(nseg * 4);
-    s.true_last = (uint32_t *)take(nseg * 4);
-    s.true_count = (uint32_t *)take(nseg * 4);
-    s.div_count = (uint32_t *)take(4);
-    s.div_list = (uint32_t *)take((size_t)div_cap * 4);
     s.flags = (uint8_t *)take(nseg);
+    s.pending = (uint32_t *)take((size_t)pending_cap * 4);
+    s.pending_a = (uint32_t *)take((size_t)pending_cap * 4);
+    s.div_list = (uint32_t *)take((size_t)div_cap * 4);
     s.stash = positions ? (uint32_t *)take(nseg * kStashCap * 12) : nullptr;
     s.nrec = positions ? (uint32_t *)take(nseg * 4) : nullptr;
     s.bytes = off;
-    s.base = base;
 }
 
 void record_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+using EmitFn = void (*)(EmitParams);
+EmitFn emit_fn(int warps) {
+    switch (warps) {
+        case 8: return emit_kernel<256>;
+        case 16: return emit_kernel<512>;
+        case 24: return emit_kernel<768>;
+        case 32: return emit_kernel<1024>;
+        default: return nullptr;
+    }
+}
 
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov) {
@@ -919,23 +1011,26 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     Plan pl;
     int rc = make_plan(d, total, positions, ov, pl);
     if (rc) return rc;
-    const uint64_t nblocks = (pl.nseg + kResolveThreads - 1) / kResolveThreads;
+    const uint64_t nblocks = (uint64_t)pl.grid;
+    const uint32_t pending_cap = (uint32_t)nblocks + 4096u;
     const uint32_t div_cap = 4096;
     Scratch s;
-    carve(s, pl.nseg, nblocks, positions, div_cap, nullptr);
+    carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, nullptr);
     void *mem = nullptr;
     DNA_CUDA(cudaMallocAsync(&mem, s.bytes, stream));
-    carve(s, pl.nseg, nblocks, positions, div_cap, (uint8_t *)mem);
-    cudaError_t e = cudaMemsetAsync(s.div_count, 0, 4, stream);
+    carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, (uint8_t *)mem);
+    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 16, stream);
 
     ScanParams sp;
     sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
     sp.lookback = pl.lookback; sp.n_states = d->n_states; sp.reset_entry = d->reset_entry;
     sp.one = d->d_one; sp.pair = d->d_pair;
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
-    sp.stash = s.stash;
+    sp.stash = s.stash; sp.nrec = s.nrec; sp.flags = s.flags;
     sp.prefetch_tiles = pl.prefetch;
-    sp.nrec = s.nrec;
+    sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap; sp.pending_a = s.pending_a;
+    sp.div_list = s.div_list; sp.div_cap = div_cap;
+    sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.out_count = out_count;
     sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
     sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
 
@@ -956,32 +1051,14 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         std::lock_guard<std::mutex> lk(g_prof_mu);
         g_prof_pending.push_back({ev0, ev1});
     }
-    ResolveParams rp;
-    rp.abase = abase; rp.lo = shift; rp.hi = total; rp.seg_bytes = pl.seg_bytes; rp.nseg = pl.nseg;
-    rp.one = d->d_one; rp.reset_entry = d->reset_entry;
-    rp.spec_start = s.spec_start; rp.last_state = s.last_state; rp.count = s.count;
-    rp.true_start = s.true_start; rp.true_last = s.true_last; rp.true_count = s.true_count;
-    rp.flags = s.flags; rp.block_sum = s.block_sum;
-    rp.div_list = s.div_list; rp.div_count = s.div_count; rp.div_cap = div_cap;
-    rp.stash = s.stash; rp.nrec = s.nrec;
-    if (e == cudaSuccess) {
-        resolve_kernel<<<(unsigned)nblocks, kResolveThreads, 0, stream>>>(rp);
-        e = cudaGetLastError();
-        record_launch();
-    }
-    if (e == cudaSuccess) {
-        finalize_kernel<<<1, 1024, 0, stream>>>(rp, nblocks, s.block_off, out_count);
-        e = cudaGetLastError();
-        record_launch();
-    }
     if (e == cudaSuccess && positions) {
         EmitParams ep;
         ep.abase = abase; ep.lo = shift; ep.hi = total; ep.seg_bytes = pl.seg_bytes; ep.nseg = pl.nseg;
-        ep.one = d->d_one; ep.reset_entry = d->reset_entry;
-        ep.true_start = s.true_start; ep.true_count = s.true_count; ep.stash = s.stash;
-        ep.nrec = s.nrec;
-        ep.flags = s.flags; ep.block_off = s.block_off; ep.out = out_positions; ep.cap = cap;
-        emit_kernel<<<(unsigned)nblocks, kResolveThreads, 0, stream>>>(ep);
+        ep.one = d->d_one; ep.reset_entry = d->reset_entry; ep.n_states = d->n_states;
+        ep.last_state = s.last_state; ep.count = s.count; ep.stash = s.stash; ep.nrec = s.nrec;
+        ep.flags = s.flags; ep.cta_off = s.cta_off; ep.out = out_positions; ep.cap = cap;
+        const size_t esmem = d->n_states * 4u <= 8192u ? (size_t)d->n_states * 16 : 0;
+        emit_fn(pl.warps)<<<pl.grid, pl.warps * 32, esmem, stream>>>(ep);
         e = cudaGetLastError();
         record_launch();
     }
