@@ -64,6 +64,7 @@ std::atomic<int> g_profile{0};
 std::mutex g_prof_mu;
 struct ProfRec { cudaEvent_t a, b; };
 std::vector<ProfRec> g_prof_pending;
+std::vector<ProfRec> g_prof_free;   // recorded pairs are reused
 double g_prof_ms = 0.0;
 uint64_t g_prof_calls = 0;
 
@@ -725,31 +726,58 @@ struct EmitParams {
     uint64_t cap;
 };
 
-// One block per scan block (same chunks). Each chunk's output offset is its block's
-// offset plus the block-exclusive prefix of the chunk counts. Recorded hit rows are
-// spread over all threads of the block; each is re-walked from its recorded start state
-// and its accepting positions written in order. Flagged or overflowing chunks are
-// rescanned from their true start (the previous chunk's last state).
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) emit_kernel(EmitParams p) {
-    __shared__ unsigned long long s_off[THREADS];
-    __shared__ uint32_t s_slot[THREADS + 1];
-    __shared__ unsigned long long wsum[THREADS / 32];
-    __shared__ uint32_t wsum2[THREADS / 32];
-    extern __shared__ uint32_t one_s[];
-    const uint32_t tid = threadIdx.x;
-    const uint64_t c = (uint64_t)blockIdx.x * THREADS + tid;
-    const bool act = c < p.nseg;
-    const uint32_t *one = p.one;
-    if (p.n_states * 4u <= 8192u) {   // small tables (<= 32 KB): copy to shared memory
-        for (uint32_t i = tid; i < p.n_states * 4u; i += THREADS) one_s[i] = p.one[i];
-        one = one_s;
+constexpr int kEmitWalkers = 256;    // threads of an extraction block that walk rows
+constexpr int kEmitRowPitch = 144;   // 128-byte row + 16 bytes: conflict-free 16-byte stores
+constexpr int kEmitRecs = 512;       // hit-row records of a block cached in shared memory
+
+// Copies aligned offsets [rs, rs + 128) of the sequence into a shared row slot with eight
+// independent 16-byte loads (a granule is read only if it starts before hi).
+__device__ __forceinline__ void stage_row(uint8_t *slot, const uint8_t *abase, uint64_t rs, uint64_t hi) {
+    uint4 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint64_t g = rs + 16u * j;
+        v[j] = g < hi ? *reinterpret_cast<const uint4 *>(abase + g) : make_uint4(0, 0, 0, 0);
     }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(slot + 16 * j) = v[j];
+}
+
+// One block per scan block, one thread per chunk. Each chunk's output offset is its block's
+// offset plus the block-exclusive prefix of the chunk counts. The recorded hit rows are
+// spread over the first kEmitWalkers threads: each stages a row in its shared slot and
+// walks it from the recorded start state, writing the accepting positions in order.
+// Flagged or overflowing chunks are rescanned row by row from their true start (the
+// previous chunk's last state). The walk maps each byte through a 256-entry class table
+// (A, C, T, G -> code, anything else -> 4) and a five-column transition table whose fifth
+// column is the reset symbol.
+__global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_in_smem) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ unsigned long long wsum[32];
+    __shared__ uint32_t wsum2[32];
+    __shared__ uint8_t cls[256];
+    __shared__ uint8_t s_rescan[1024];
+    __shared__ uint4 s_rec[kEmitRecs];   // (tile, start state, count before, chunk index)
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    // dynamic shared memory: [row slots: walkers x pitch][offsets: nthr x 8][slots: nthr+1 x 4][table]
+    unsigned long long *s_off = reinterpret_cast<unsigned long long *>(dsm + kEmitWalkers * kEmitRowPitch);
+    uint32_t *s_slot = reinterpret_cast<uint32_t *>(s_off + nthr);
+    uint32_t *tab5 = s_slot + nthr + 1;
+    if (tid < 256) {
+        const uint32_t c = (tid >> 1) & 3u;
+        cls[tid] = byte_is_base(tid) ? (uint8_t)c : (uint8_t)4;
+    }
+    if (tab5_in_smem)
+        for (uint32_t i = tid; i < p.n_states * 5u; i += nthr) {
+            const uint32_t q = i / 5u, col = i - q * 5u;
+            tab5[i] = col < 4 ? p.one[q * 4u + col] : p.reset_entry;
+        }
+    const uint64_t c = (uint64_t)blockIdx.x * nthr + tid;
+    const bool act = c < p.nseg;
     const unsigned long long v = act ? p.count[c] : 0u;
     const uint32_t nr = act ? p.nrec[c] : 0u;
     const bool rescan = act && v > 0 && (p.flags[c] != 0 || nr > (uint32_t)kStashCap);
     const uint32_t rows = (act && !rescan) ? nr : 0u;
-    // block-exclusive scans of counts and of hit rows
     unsigned long long x = v;
     uint32_t y = rows;
     for (int o = 1; o < 32; o <<= 1) {
@@ -759,45 +787,103 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitParams p) {
     }
     if ((tid & 31) == 31) { wsum[tid >> 5] = x; wsum2[tid >> 5] = y; }
     __syncthreads();
-    unsigned long long bx = 0;
-    uint32_t by = 0;
-    for (uint32_t i = 0; i < (tid >> 5); ++i) { bx += wsum[i]; by += wsum2[i]; }
+    if (tid < 32) {
+        const uint32_t nw = nthr >> 5;
+        unsigned long long a = tid < nw ? wsum[tid] : 0ull;
+        uint32_t bb = tid < nw ? wsum2[tid] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long aa = __shfl_up_sync(0xFFFFFFFFu, a, o);
+            const uint32_t ba = __shfl_up_sync(0xFFFFFFFFu, bb, o);
+            if (tid >= (uint32_t)o) { a += aa; bb += ba; }
+        }
+        if (tid < nw) { wsum[tid] = a; wsum2[tid] = bb; }
+    }
+    __syncthreads();
+    const unsigned long long bx = (tid >> 5) ? wsum[(tid >> 5) - 1] : 0ull;
+    const uint32_t by = (tid >> 5) ? wsum2[(tid >> 5) - 1] : 0u;
     const unsigned long long off = p.cta_off[blockIdx.x] + bx + x - v;
     s_off[tid] = off;
     s_slot[tid] = by + y - rows;
-    if (tid == THREADS - 1) s_slot[THREADS] = by + y;
+    if (tid == nthr - 1) s_slot[nthr] = by + y;
+    s_rescan[tid] = rescan ? 1 : 0;
+    // each chunk copies its hit-row records into shared memory (first kEmitRecs rows)
+    const uint32_t slot0 = by + y - rows;
+    for (uint32_t i = 0; i < rows; ++i) {
+        if (slot0 + i >= (uint32_t)kEmitRecs) break;
+        const uint32_t *rec = p.stash + c * (kStashCap * 3) + 3 * i;
+        s_rec[slot0 + i] = make_uint4(rec[0], rec[1], rec[2], (uint32_t)tid);
+    }
     __syncthreads();
-    const uint32_t total_rows = s_slot[THREADS];
+    const uint32_t total_rows = s_slot[nthr];
+    const uint32_t *tab = tab5_in_smem ? tab5 : nullptr;
 
-    auto walk = [&](uint64_t from, uint64_t to, uint32_t q, unsigned long long o) {
-        walk_range(p.abase, from, to, p.hi, [&](uint64_t a, uint32_t byte) {
-            const uint32_t e = one_step(one, p.reset_entry, q, byte);
+    // walks bytes [k0, k1) of the row at aligned offset rs (staged in 'slot') from state q
+    auto walk_row = [&](uint8_t *slot, uint64_t rs, uint32_t k0, uint32_t k1, uint32_t q,
+                        unsigned long long &o) {
+        stage_row(slot, p.abase, rs, p.hi);
+        const uint64_t pos0 = rs - p.lo;
+        for (uint32_t k = k0; k < k1; ++k) {
+            const uint32_t cl = cls[slot[k]];
+            const uint32_t e = tab ? tab[q * 5u + cl] : (cl < 4 ? p.one[q * 4u + cl] : p.reset_entry);
             q = e & 0x7FFFFFFFu;
-            if (e >> 31) p.out[o++] = a - p.lo;
-            return o < p.cap;
-        });
+            if (e >> 31) {
+                if (o < p.cap) p.out[o] = pos0 + k;
+                ++o;
+            }
+        }
+        return q;
+    };
+    auto row_span = [&](uint64_t rs, uint64_t from, uint64_t to, uint32_t &k0, uint32_t &k1) {
+        k0 = from > rs ? (uint32_t)(from - rs) : 0u;
+        k1 = to < rs + kTile ? (uint32_t)(to - rs) : (uint32_t)kTile;
     };
     const uint64_t S = p.seg_bytes;
-    if (rescan && off < p.cap) {
-        const uint64_t b = c * S;
-        walk(b > p.lo ? b : p.lo, b + S < p.hi ? b + S : p.hi, c ? p.last_state[c - 1] : 0u, off);
-    }
-    for (uint32_t r = tid; r < total_rows; r += THREADS) {
-        // the chunk owning hit-row slot r: largest j with s_slot[j] <= r
-        uint32_t lo = 0, hi = THREADS - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (s_slot[mid] <= r) lo = mid; else hi = mid - 1;
+    // rescans (rare), by walker threads in turn
+    if (tid < kEmitWalkers) {
+        uint8_t *slot = dsm + tid * kEmitRowPitch;
+        for (uint32_t j = tid; j < nthr; j += kEmitWalkers) {
+            if (!s_rescan[j]) continue;
+            const uint64_t cj = (uint64_t)blockIdx.x * nthr + j;
+            const unsigned long long oj = s_off[j];
+            if (oj >= p.cap) continue;
+            unsigned long long o = oj;
+            const uint64_t b = cj * S;
+            const uint64_t from = b > p.lo ? b : p.lo;
+            const uint64_t to = b + S < p.hi ? b + S : p.hi;
+            uint32_t q = cj ? p.last_state[cj - 1] : 0u;
+            for (uint64_t rs = b; rs < to && o < p.cap; rs += kTile) {
+                uint32_t k0, k1;
+                row_span(rs, from, to, k0, k1);
+                q = walk_row(slot, rs, k0, k1, q, o);
+            }
         }
-        const uint32_t j = lo;
-        const uint64_t cj = (uint64_t)blockIdx.x * THREADS + j;
-        const uint32_t *rec = p.stash + cj * (kStashCap * 3) + 3 * (r - s_slot[j]);
-        const unsigned long long o = s_off[j] + rec[2];
-        if (o >= p.cap) continue;
-        const uint64_t b = cj * S;
-        const uint64_t cend = b + S < p.hi ? b + S : p.hi;
-        const uint64_t rs = b + (uint64_t)rec[0] * kTile;
-        walk(rs > p.lo ? rs : p.lo, rs + kTile < cend ? rs + kTile : cend, rec[1], o);
+        // hit rows
+        for (uint32_t r = tid; r < total_rows; r += kEmitWalkers) {
+            uint32_t lo, rec[3];
+            if (r < (uint32_t)kEmitRecs) {
+                const uint4 rr = s_rec[r];
+                rec[0] = rr.x; rec[1] = rr.y; rec[2] = rr.z; lo = rr.w;
+            } else {
+                lo = 0;
+                uint32_t hi = nthr - 1;   // largest j with s_slot[j] <= r
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_slot[mid] <= r) lo = mid; else hi = mid - 1;
+                }
+                const uint64_t cl = (uint64_t)blockIdx.x * nthr + lo;
+                const uint32_t *g = p.stash + cl * (kStashCap * 3) + 3 * (r - s_slot[lo]);
+                rec[0] = g[0]; rec[1] = g[1]; rec[2] = g[2];
+            }
+            const uint64_t cj = (uint64_t)blockIdx.x * nthr + lo;
+            unsigned long long o = s_off[lo] + rec[2];
+            if (o >= p.cap) continue;
+            const uint64_t b = cj * S;
+            const uint64_t cend = b + S < p.hi ? b + S : p.hi;
+            const uint64_t rs = b + (uint64_t)rec[0] * kTile;
+            uint32_t k0, k1;
+            row_span(rs, rs > p.lo ? rs : p.lo, rs + kTile < cend ? rs + kTile : cend, k0, k1);
+            walk_row(slot, rs, k0, k1, rec[1], o);
+        }
     }
 }
 
@@ -879,6 +965,9 @@ struct dna_dfa {
     uint32_t reset_entry = 0;
     uint32_t *d_one = nullptr;
     uint32_t *d_pair = nullptr;
+    // resident blocks per SM of each scan kernel variant with this automaton's shared
+    // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
+    std::atomic<int> per_sm[3][4][2] = {};
 };
 
 namespace {
@@ -901,6 +990,19 @@ struct Plan {
     size_t smem;
     int grid;
 };
+
+// Raises a kernel's dynamic shared-memory limit to 'bytes' once per (kernel, device).
+int ensure_smem_optin(const void *fn, int device, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == fn && d.second == device) return DNA_OK;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    done.emplace_back(fn, device);
+    return DNA_OK;
+}
 
 int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Plan &pl) {
     DeviceProps pr = device_props(d->device);
@@ -927,11 +1029,19 @@ int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Pl
     uint32_t pf = kDefaultPrefetch;
     if (ov && ov->prefetch_tiles) pf = ov->prefetch_tiles >= 255 ? 0 : ov->prefetch_tiles;
     if (pf > 64) return DNA_ERR_INVALID_ARG;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
-    if (per_sm < 1) per_sm = 1;
+    // the shared-memory opt-in is set once per kernel variant (to the device maximum),
+    // the occupancy once per automaton and variant
+    const int wi = warps == 8 ? 0 : warps == 16 ? 1 : warps == 24 ? 2 : 3;
+    std::atomic<int> &occ = const_cast<dna_dfa *>(d)->per_sm[mode][wi][pos ? 1 : 0];
+    int per_sm = occ.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        int rc = ensure_smem_optin((const void *)fn, d->device, optin - scan_static_smem(warps));
+        if (rc) return rc;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (per_sm < 1) per_sm = 1;
+        occ.store(per_sm, std::memory_order_relaxed);
+    }
     uint64_t S;
     if (ov && ov->chunk_bytes) {
         if (ov->chunk_bytes % kTile) return DNA_ERR_INVALID_ARG;
@@ -981,17 +1091,6 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
 
 void record_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
-using EmitFn = void (*)(EmitParams);
-EmitFn emit_fn(int warps) {
-    switch (warps) {
-        case 8: return emit_kernel<256>;
-        case 16: return emit_kernel<512>;
-        case 24: return emit_kernel<768>;
-        case 32: return emit_kernel<1024>;
-        default: return nullptr;
-    }
-}
-
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov) {
     if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
@@ -1037,8 +1136,14 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = g_profile.load(std::memory_order_relaxed) != 0;
     if (prof && e == cudaSuccess) {
-        cudaEventCreate(&ev0);
-        cudaEventCreate(&ev1);
+        {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            if (!g_prof_free.empty()) {
+                ev0 = g_prof_free.back().a; ev1 = g_prof_free.back().b;
+                g_prof_free.pop_back();
+            }
+        }
+        if (!ev0) { cudaEventCreate(&ev0); cudaEventCreate(&ev1); }
         cudaEventRecord(ev0, stream);
     }
     if (e == cudaSuccess) {
@@ -1057,8 +1162,15 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         ep.one = d->d_one; ep.reset_entry = d->reset_entry; ep.n_states = d->n_states;
         ep.last_state = s.last_state; ep.count = s.count; ep.stash = s.stash; ep.nrec = s.nrec;
         ep.flags = s.flags; ep.cta_off = s.cta_off; ep.out = out_positions; ep.cap = cap;
-        const size_t esmem = d->n_states * 4u <= 8192u ? (size_t)d->n_states * 16 : 0;
-        emit_fn(pl.warps)<<<pl.grid, pl.warps * 32, esmem, stream>>>(ep);
+        const uint32_t cpb = (uint32_t)pl.warps * 32u;   // one extraction thread per chunk
+        const uint32_t tab5_smem = d->n_states * 5u <= 4096u ? 1u : 0u;
+        const size_t esmem = (size_t)kEmitWalkers * kEmitRowPitch + (size_t)cpb * 8 + (size_t)(cpb + 1) * 4 +
+                             (tab5_smem ? (size_t)d->n_states * 20 : 0);
+        const size_t optin = device_props(d->device).smem_optin;
+        // the extraction kernel's static shared memory is about 10 KB; 16 KB is reserved
+        int rc2 = ensure_smem_optin((const void *)emit_kernel, d->device, (optin ? optin : 232448) - 16384);
+        if (rc2) e = cudaErrorInvalidValue;
+        else emit_kernel<<<pl.grid, cpb, esmem, stream>>>(ep, tab5_smem);
         e = cudaGetLastError();
         record_launch();
     }
@@ -1202,8 +1314,7 @@ extern "C" int dna_profile_read(dna_profile_t *out, int reset) {
             g_prof_ms += ms;
             ++g_prof_calls;
         }
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
+        g_prof_free.push_back(r);
     }
     g_prof_pending.clear();
     out->scan_kernel_ms = g_prof_ms;
