@@ -126,6 +126,29 @@ int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t 
              uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity);
 
 /*
+ * dna_scan_count_static -- the count of dna_scan, computed without allocating memory.
+ *   Same arguments and result as dna_scan with out_positions = NULL. The paper has no
+ *   counterpart: this entry point exists for callers that cannot let a library
+ *   allocate device memory while they run -- for example a server that reserves all of
+ *   the GPU's memory up front and hands out fixed buffers, or code that must not trigger
+ *   the implicit synchronisation an allocation can cause. Instead of stream-ordered
+ *   scratch, the scan uses one fixed 4 MiB array in device memory that the library
+ *   declares at file scope; every GPU that loads the library holds it until the process
+ *   exits.
+ *   Limits: len <= 2^36 bytes (64 GiB); a length or automaton whose chunk bookkeeping
+ *   would not fit in the 4 MiB array returns DNA_ERR_CAPACITY before any work is queued.
+ *   Set-up: the first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   Sharing: all calls use the same array, which keeps the previous call's contents;
+ *   calls that overlap on the GPU (different streams, or no ordering between them)
+ *   race on it and give wrong counts. Order the calls, e.g. issue them on one stream.
+ *   No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_CAPACITY, DNA_ERR_CUDA.
+ */
+int dna_scan_count_static(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
+                          dna_stream_t stream, uint64_t *out_count);
+
+/*
  * Plan override for dna_scan_planned (tests sweep it: results must not depend on it).
  *   chunk_bytes    bytes per chunk (one chunk per GPU lane); multiple of 128, >= 128;
  *                  0 = automatic.

@@ -23,6 +23,7 @@ PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE = 0, 1, 2, 3
 
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
+    "dna_scan_count_static",
     "dna_status_string", "dna_compile_regex", "dna_compile_kmers", "dna_free_host",
     "dna_profile_enable", "dna_profile_read",
 ]
@@ -84,6 +85,8 @@ def lib():
         L.dna_scan.restype = i32
         L.dna_scan_planned.argtypes = [p, p, u64, p, p, p, u64, ctypes.POINTER(_Plan)]
         L.dna_scan_planned.restype = i32
+        L.dna_scan_count_static.argtypes = [p, p, u64, p, p]
+        L.dna_scan_count_static.restype = i32
         L.dna_scan_batch.argtypes = [p, u32, p, p, u32, p, p]
         L.dna_scan_batch.restype = i32
         L.dna_status_string.argtypes = [i32]
@@ -269,6 +272,20 @@ def scan_ptr(dfa: Dfa, ptr: int, length: int, out_count_ptr: int, stream_handle:
     """Raw-pointer form of dna_scan (device or host-mapped pointers)."""
     _check(lib().dna_scan(dfa.handle, ptr, length, stream_handle, out_count_ptr,
                           positions_ptr, capacity), "dna_scan")
+
+
+def scan_count_static(dfa: Dfa, seq, stream=None, out_count=None):
+    """dna_scan_count_static: the count of dna_scan without any device allocation (the
+    library's fixed scratch array is used; see include/dna_dfa.h for its limits)."""
+    import torch
+    if not (isinstance(seq, torch.Tensor) and seq.is_cuda and seq.dtype == torch.uint8):
+        raise TypeError("seq must be a CUDA uint8 tensor")
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=seq.device)
+    _check(lib().dna_scan_count_static(dfa.handle, seq.data_ptr(), seq.numel(),
+                                       _stream_handle(stream), out_count.data_ptr()),
+           "dna_scan_count_static")
+    return out_count
 
 
 def scan_batch(dfas, seqs, stream=None, out=None):

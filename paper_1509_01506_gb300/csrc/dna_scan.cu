@@ -1275,6 +1275,86 @@ extern "C" int dna_scan_planned(const dna_dfa *dfa, const uint8_t *seq, uint64_t
                      positions_capacity, plan);
 }
 
+// ------------------------------------------------------- allocation-free count
+
+// Scratch of dna_scan_count_static: one array per process, present on every device that
+// loads this library, for its lifetime. Host code never uses the name as an address; the
+// device address comes from cudaGetSymbolAddress, once per device.
+constexpr size_t kStaticScratchBytes = 4u << 20;     // 4 MiB
+constexpr uint64_t kStaticMaxLen = 1ull << 36;       // 64 GiB of sequence per call
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+std::vector<void *> g_static_addr;   // per device: device address of g_static_scratch
+
+// Set-up on the first call for a device (that device is current): looks up the device
+// address of the scratch array. No allocation is made.
+int static_scratch_address(int dev, void **out) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if ((int)g_static_addr.size() <= dev) g_static_addr.resize(dev + 1, nullptr);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) return e != cudaSuccess ? cuda_status(e) : DNA_ERR_CUDA;
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return DNA_OK;
+}
+
+}  // namespace
+
+extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint64_t len,
+                                     dna_stream_t stream_h, uint64_t *out_count) {
+    cudaStream_t stream = (cudaStream_t)stream_h;
+    if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
+    if (len > kStaticMaxLen) return DNA_ERR_CAPACITY;
+    int cur_dev = -1;
+    DNA_CUDA(cudaGetDevice(&cur_dev));
+    if (cur_dev != d->device) return DNA_ERR_INVALID_ARG;
+    void *base = nullptr;
+    int rc = static_scratch_address(cur_dev, &base);
+    if (rc) return rc;
+    if (len == 0) {
+        write_zero_kernel<<<1, 1, 0, stream>>>(out_count);
+        record_launch();
+        return cuda_status(cudaGetLastError());
+    }
+    const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
+    const uint8_t *abase = seq - shift;
+    const uint64_t total = len + shift;
+    Plan pl;
+    rc = make_plan(d, total, false, nullptr, pl);
+    if (rc) return rc;
+    const uint64_t nblocks = (uint64_t)pl.grid;
+    const uint32_t pending_cap = (uint32_t)nblocks + 4096u;
+    const uint32_t div_cap = 4096;
+    Scratch s;
+    carve(s, pl.nseg, nblocks, false, pending_cap, div_cap, nullptr);
+    if (s.bytes > kStaticScratchBytes) return DNA_ERR_CAPACITY;
+    carve(s, pl.nseg, nblocks, false, pending_cap, div_cap, (uint8_t *)base);
+    // the counters the kernel expects at zero; everything else is written before it is read
+    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 16, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    ScanParams sp;
+    sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
+    sp.lookback = pl.lookback; sp.n_states = d->n_states; sp.reset_entry = d->reset_entry;
+    sp.one = d->d_one; sp.pair = d->d_pair;
+    sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
+    sp.stash = nullptr; sp.nrec = nullptr; sp.flags = s.flags;
+    sp.prefetch_tiles = pl.prefetch;
+    sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap; sp.pending_a = s.pending_a;
+    sp.div_list = s.div_list; sp.div_cap = div_cap;
+    sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.out_count = out_count;
+    sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
+    sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
+    scan_fn(pl.mode, pl.warps, false)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);
+    record_launch();
+    return cuda_status(cudaGetLastError());
+}
+
 extern "C" int dna_scan_batch(const dna_dfa *const *dfas, uint32_t n_dfas, const uint8_t *const *seqs,
                               const uint64_t *lens, uint32_t n_seqs, dna_stream_t stream,
                               uint64_t *out_counts) {
