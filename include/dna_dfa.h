@@ -126,6 +126,22 @@ int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t 
              uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity);
 
 /*
+ * dna_scan_host -- dna_scan on a sequence in host memory, with host-memory results.
+ *   seq_host        host pointer to len bytes (pinned memory copies fastest).
+ *   count_host      host pointer: receives the count.
+ *   positions_host  host pointer or NULL; receives the first min(count,
+ *                   positions_capacity) positions, as dna_scan's out_positions.
+ * The call copies the sequence to a device buffer it allocates on 'stream', scans it,
+ * copies the results back and returns after the stream has finished them (it is
+ * synchronous with respect to the host). Returns DNA_ERR_CAPACITY when the count
+ * exceeds positions_capacity (count_host then holds the true count and the smallest
+ * positions_capacity positions were written). Other errors as dna_scan, plus
+ * DNA_ERR_NOMEM when the device buffer cannot be allocated.
+ */
+int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64_t len, dna_stream_t stream,
+                  uint64_t *count_host, uint64_t *positions_host, uint64_t positions_capacity);
+
+/*
  * dna_scan_count_static -- the count of dna_scan, computed without allocating memory.
  *   Same arguments and result as dna_scan with out_positions = NULL. The paper has no
  *   counterpart: this entry point exists for callers that cannot let a library

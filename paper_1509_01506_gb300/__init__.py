@@ -23,7 +23,7 @@ PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE = 0, 1, 2, 3
 
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
-    "dna_scan_count_static",
+    "dna_scan_count_static", "dna_scan_host",
     "dna_status_string", "dna_compile_regex", "dna_compile_kmers", "dna_free_host",
     "dna_profile_enable", "dna_profile_read",
 ]
@@ -87,6 +87,8 @@ def lib():
         L.dna_scan_planned.restype = i32
         L.dna_scan_count_static.argtypes = [p, p, u64, p, p]
         L.dna_scan_count_static.restype = i32
+        L.dna_scan_host.argtypes = [p, p, u64, p, p, p, u64]
+        L.dna_scan_host.restype = i32
         L.dna_scan_batch.argtypes = [p, u32, p, p, u32, p, p]
         L.dna_scan_batch.restype = i32
         L.dna_status_string.argtypes = [i32]
@@ -286,6 +288,41 @@ def scan_count_static(dfa: Dfa, seq, stream=None, out_count=None):
                                        _stream_handle(stream), out_count.data_ptr()),
            "dna_scan_count_static")
     return out_count
+
+
+def scan_host(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None,
+              stream=None, out_count=None, out_positions=None):
+    """dna_scan_host: scans a host uint8 array (a numpy array or a CPU tensor, pinned for
+    the fastest copy); returns (count, positions array or None) in host memory. The call
+    is synchronous. A count above the capacity raises DnaError (DNA_ERR_CAPACITY)."""
+    import torch
+    if isinstance(seq, np.ndarray):
+        if seq.dtype != np.uint8 or not seq.flags.c_contiguous:
+            raise TypeError("seq must be a contiguous uint8 array")
+        ptr, n = seq.ctypes.data, seq.size
+    elif isinstance(seq, torch.Tensor) and not seq.is_cuda and seq.dtype == torch.uint8:
+        if not seq.is_contiguous():
+            raise ValueError("seq must be contiguous")
+        ptr, n = seq.data_ptr(), seq.numel()
+    else:
+        raise TypeError("seq must be a host uint8 array or CPU tensor")
+    if out_count is None:
+        out_count = np.zeros(1, dtype=np.uint64)
+    cptr = out_count.ctypes.data if isinstance(out_count, np.ndarray) else out_count.data_ptr()
+    pos_ptr, cap = None, 0
+    if positions:
+        if out_positions is None:
+            cap = int(capacity if capacity is not None else max(1024, n // 256))
+            out_positions = np.empty(cap, dtype=np.uint64)
+        else:
+            cap = (out_positions.size if isinstance(out_positions, np.ndarray)
+                   else out_positions.numel()) if capacity is None else int(capacity)
+        pos_ptr = (out_positions.ctypes.data if isinstance(out_positions, np.ndarray)
+                   else out_positions.data_ptr())
+    _check(lib().dna_scan_host(dfa.handle, ptr, n, _stream_handle(stream), cptr, pos_ptr, cap),
+           "dna_scan_host")
+    c = int(out_count[0])
+    return c, (out_positions[:c] if positions else None)
 
 
 def scan_batch(dfas, seqs, stream=None, out=None):

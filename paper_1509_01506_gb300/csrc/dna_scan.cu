@@ -1268,6 +1268,44 @@ extern "C" int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dn
                      positions_capacity, nullptr);
 }
 
+extern "C" int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64_t len,
+                             dna_stream_t stream_h, uint64_t *count_host, uint64_t *positions_host,
+                             uint64_t positions_capacity) {
+    if (!dfa || !count_host || (len > 0 && !seq_host)) return DNA_ERR_INVALID_ARG;
+    if (positions_capacity > 0 && !positions_host) return DNA_ERR_INVALID_ARG;
+    if (len > (1ull << 40) || positions_capacity > (1ull << 40)) return DNA_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_h;
+    // one stream-ordered buffer: [count (8 B)][positions][sequence], the sequence
+    // 16-byte aligned so the scan starts on a full granule
+    const uint64_t cap = positions_host ? positions_capacity : 0;
+    const size_t seq_off = align_up(8 + (size_t)cap * 8, 256);
+    void *mem = nullptr;
+    DNA_CUDA(cudaMallocAsync(&mem, seq_off + (size_t)len + 16, stream));
+    uint8_t *base = (uint8_t *)mem;
+    uint64_t *d_count = (uint64_t *)base;
+    uint64_t *d_pos = cap ? (uint64_t *)(base + 8) : nullptr;
+    uint8_t *d_seq = base + seq_off;
+    cudaError_t e = len ? cudaMemcpyAsync(d_seq, seq_host, len, cudaMemcpyHostToDevice, stream) : cudaSuccess;
+    int rc = DNA_OK;
+    if (e == cudaSuccess) rc = scan_impl(dfa, d_seq, len, stream, d_count, d_pos, cap, nullptr);
+    if (e == cudaSuccess && rc == DNA_OK) {
+        e = cudaMemcpyAsync(count_host, d_count, 8, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess && cap) {
+            const uint64_t n = *count_host < cap ? *count_host : cap;
+            if (n) {
+                e = cudaMemcpyAsync(positions_host, d_pos, n * 8, cudaMemcpyDeviceToHost, stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            }
+        }
+    }
+    cudaError_t ef = cudaFreeAsync(mem, stream);
+    if (e == cudaSuccess) e = ef;
+    if (rc != DNA_OK) return rc;
+    if (e != cudaSuccess) return cuda_status(e);
+    return cap && *count_host > cap ? DNA_ERR_CAPACITY : DNA_OK;
+}
+
 extern "C" int dna_scan_planned(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
                                 dna_stream_t stream, uint64_t *out_count, uint64_t *out_positions,
                                 uint64_t positions_capacity, const dna_plan *plan) {

@@ -256,6 +256,30 @@ def test_invalid_arguments_are_rejected():
     assert ei.value.code == -3
 
 
+def test_host_buffer_entry_point():
+    """dna_scan_host: host sequence in, host count and positions out, same results as
+    the oracle; a capacity below the count reports DNA_ERR_CAPACITY with the true count
+    and the smallest positions."""
+    pat = synth.CONFIG2_REGEX
+    seq = noisy_markov(21, 3 * MiB + 101)
+    t, a = oracle.compile_regex(pat)
+    want_c, want_p = oracle.run(t, a, seq)
+    dfa = dna.Dfa.from_regex(pat)
+    c, p = dna.scan_host(dfa, seq, positions=True, capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p.astype(np.int64), want_p)
+    pinned = torch.from_numpy(seq).pin_memory()
+    c2, _ = dna.scan_host(dfa, pinned)
+    assert c2 == want_c
+    out_c = np.zeros(1, np.uint64)
+    out_p = np.zeros(7, np.uint64)
+    with pytest.raises(dna.DnaError) as ei:
+        dna.scan_host(dfa, seq, positions=True, out_count=out_c, out_positions=out_p)
+    assert ei.value.code == -3
+    assert int(out_c[0]) == want_c and np.array_equal(out_p.astype(np.int64), want_p[:7])
+    c0, p0 = dna.scan_host(dfa, np.zeros(0, np.uint8), positions=True, capacity=4)
+    assert c0 == 0 and p0.size == 0
+
+
 # ------------------------------------------------------ full-size workloads
 
 def test_plain_markov_full_size_launch_config():
