@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=10)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-percall", action="store_true")
     return ap.parse_args()
 
 
@@ -187,6 +190,115 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+BATCH_WORKLOAD = ("batched: 4,096 i.i.d. A/C/G/T sequences, lengths log-uniform 1 KiB..16 MiB (seed 3), "
+                  "x 64 minimised motif regexes of 5-60 states; per-(sequence, automaton) exact counts")
+
+
+def lds_lookup_peak(sms: int, mhz: float) -> float:
+    """Shared-memory lookups per second the SMs can issue: one 32-lane LDS wavefront per
+    SM per clock (bank-conflict free)."""
+    return sms * 32 * mhz * 1e6
+
+
+def bench_batched(args, dna, torch, stream, clocks_mhz):
+    """The batched configuration: one plan (autotuned, graph-captured), K timed runs;
+    then the same pairs through one dna_scan call each."""
+    import synth
+    buf, offs, regexes = synth.batched(n_states=lambda r: dna.compile_regex(r)[0].shape[0])
+    n_s = offs.size - 1
+    lens = [int(offs[i + 1] - offs[i]) for i in range(n_s)]
+    total = int(offs[-1])
+    dbuf = torch.empty(total + 256 * n_s, dtype=torch.uint8, device="cuda")
+    hbuf = torch.from_numpy(buf)
+    starts, pos = [], 0
+    for i in range(n_s):
+        dbuf[pos:pos + lens[i]].copy_(hbuf[int(offs[i]):int(offs[i + 1])])
+        starts.append(dbuf.data_ptr() + pos)
+        pos += (lens[i] + 255) // 256 * 256
+    del hbuf, buf
+    dfas = [dna.Dfa.from_regex(r) for r in regexes]
+    states = [d.info().n_states for d in dfas]
+    t0 = time.perf_counter()
+    plan = dna.Batch(dfas, starts, lens=lens, autotune=True, use_graph=True, stream=stream)
+    tune_s = time.perf_counter() - t0
+    info = plan.info()
+    out = torch.empty((n_s, len(dfas)), dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        plan.run(out, stream=stream)
+    torch.cuda.synchronize()
+    dna.profile_read(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.batch_runs):
+        plan.run(out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = dna.profile_read(reset=True)["kernel_launches"]
+    ms = e0.elapsed_time(e1) / args.batch_runs
+    # kernel times from a separate pass with events around each launch (a graph replay
+    # records no per-launch events, so this pass uses the same plan without a graph)
+    plain = dna.Batch(dfas, starts, lens=lens, chunk_bases=info.chunk_bases,
+                      warps_per_cta=info.warps_per_cta, stream=stream)
+    plain.run(out, stream=stream)
+    torch.cuda.synchronize()
+    dna.profile_read(reset=True)
+    dna.profile_enable(True)
+    for _ in range(3):
+        plain.run(out, stream=stream)
+    torch.cuda.synchronize()
+    dna.profile_enable(False)
+    prof = dna.profile_read(reset=True)
+    plain.free()
+    k_ms = prof["batch_kernel_ms"] / max(1, prof["batch_kernel_calls"])
+    i_ms = prof["ingest_kernel_ms"] / max(1, prof["ingest_kernel_calls"])
+    counts = out.cpu().numpy()
+    res = {
+        "workload": BATCH_WORKLOAD, "n_seqs": n_s, "n_dfas": len(dfas), "bytes": total,
+        "states_min": min(states), "states_max": max(states),
+        "plan": {"chunk_bases": info.chunk_bases, "warps_per_cta": info.warps_per_cta, "grid": info.grid,
+                 "groups_per_task": info.groups_per_task, "n_fast": info.n_fast, "n_slow": info.n_slow,
+                 "autotune_s": tune_s, "graph": True},
+        "runs": args.batch_runs, "ms_per_run": ms, "gpu_launches_per_run": launches / args.batch_runs,
+        "unique_gbs": total / (ms * 1e-3) / 1e9,
+        "seq_x_dfa_gbs": total * len(dfas) / (ms * 1e-3) / 1e9,
+        "ingest_ms": i_ms, "batch_kernel_ms": k_ms,
+        "total_matches": int(counts.sum()),
+    }
+    peak = lds_lookup_peak(torch.cuda.get_device_properties(0).multi_processor_count, clocks_mhz or 2070.0)
+    lookups = total * info.n_fast * 0.5    # one two-symbol lookup per 2 bases per automaton
+    res["roofline"] = {"bound": "alu", "unit": "lookups/s", "achieved": lookups / (k_ms * 1e-3),
+                       "peak": peak, "frac": lookups / (k_ms * 1e-3) / peak,
+                       "peak_source": "SMs x 32 shared-memory lookups per clock x SM clock (median under load)"}
+    if not args.no_percall:
+        # the same pairs, one dna_scan (count only) per (sequence, automaton)
+        cnt = torch.empty((n_s, len(dfas)), dtype=torch.int64, device="cuda")
+        sh = int(stream.cuda_stream)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        c0.record(stream)
+        base = cnt.data_ptr()
+        for si in range(n_s):
+            for k, d in enumerate(dfas):
+                dna.scan_ptr(d, starts[si], lens[si], base + 8 * (si * len(dfas) + k), sh)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        pc_ms = c0.elapsed_time(c1)
+        same = bool(torch.equal(cnt, out))
+        res["per_call"] = {"calls": n_s * len(dfas), "ms": pc_ms, "wall_s": wall,
+                           "seq_x_dfa_gbs": total * len(dfas) / (pc_ms * 1e-3) / 1e9,
+                           "identical_counts": same}
+        res["batched_over_per_call"] = pc_ms / ms
+    plan.free()
+    del dbuf
+    torch.cuda.empty_cache()
+    return res
+
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -301,6 +413,10 @@ def main():
                "sample": f"{done / MiB:.0f} MiB scanned as 32 MiB slices of the 256 MiB workload "
                          f"(count + positions), single thread"}
 
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = bench_batched(args, dna, torch, stream, clocks.get("sm_mhz"))
+
     info = dfa.info()
     if rank == 0:
         line = {
@@ -320,6 +436,7 @@ def main():
                     "d2h_bytes_per_step": 8 + 8 * n_matches, "ms_per_step": e2e_ms,
                     "api": "dna_scan_host (pinned host buffers, synchronous)"},
             "gpu_launches": launches,
+            "batched": batched,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

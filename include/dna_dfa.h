@@ -190,13 +190,81 @@ int dna_scan_planned(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
                      uint64_t positions_capacity, const dna_plan *plan);
 
 /*
- * dna_scan_batch -- counts every (sequence, automaton) pair of a batch in one queued
- * launch sequence (the batched path).
+ * Batched path: the counts of every (sequence, automaton) pair of a batch, computed by
+ * one persistent kernel after one ingest kernel (the chunked scan of Sec. III-A applied
+ * to many inputs and many automata at once; the paper runs one automaton over one input).
+ * Automata with a definite depth <= 64 (dfa_info) and at most ~90 states run in the
+ * persistent kernel; the others are scanned with dna_scan, one call per pair, inside
+ * the same queued work.
+ *
+ * dna_batch_create -- builds a reusable plan for a fixed set of automata and sequences.
  *   dfas     host array of n_dfas handles (all loaded on the current device).
- *   seqs     host array of n_seqs device pointers; lens host array of their lengths.
- *   out_counts device uint64 [n_seqs][n_dfas], row-major; element (s, d) receives the
- *            count of automaton d over sequence s.
+ *   seqs     host array of n_seqs device pointers; lens host array of their lengths. The
+ *            plan keeps the pointers: the sequences must stay allocated (their contents
+ *            may change between runs) until dna_batch_free.
+ *   opts     NULL for defaults, or:
+ *              chunk_bases    chunk length in bases, a multiple of 512 (<= 131072);
+ *                             0 = 4096, or the autotuner's choice;
+ *              warps_per_cta  8, 16 or 24; 0 = the most that fit;
+ *              autotune       1 = time each (chunk length, warps) candidate on the
+ *                             batch's own data during create and keep the fastest
+ *                             (only when chunk_bases and warps_per_cta are 0);
+ *              use_graph      1 = dna_batch_run captures the queued work into a CUDA
+ *                             graph on its first call for a given out_counts pointer
+ *                             and replays it afterwards.
+ *   stream   used for the set-up copies (and the autotuner's runs); create returns
+ *            after they have finished.
+ *   out      receives the plan; the library owns it until dna_batch_free.
+ * The plan allocates device memory for the packed copy of the sequences (one 2-bit code
+ * per base plus one flag byte per 512 bases, about 0.25 bytes per base).
  * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_NOMEM, DNA_ERR_CUDA, DNA_ERR_CAPACITY.
+ */
+typedef struct {
+    uint32_t chunk_bases;
+    uint32_t warps_per_cta;
+    uint32_t autotune;
+    uint32_t use_graph;
+} dna_batch_opts;
+
+typedef struct dna_batch dna_batch; /* opaque */
+
+int dna_batch_create(const dna_dfa *const *dfas, uint32_t n_dfas,
+                     const uint8_t *const *seqs, const uint64_t *lens, uint32_t n_seqs,
+                     const dna_batch_opts *opts, dna_stream_t stream, dna_batch **out);
+
+/*
+ * dna_batch_run -- queues the batch on 'stream'.
+ *   out_counts  device uint64 [n_seqs][n_dfas], row-major; element (s, d) receives the
+ *               count of automaton d over sequence s (the dna_scan count).
+ * Asynchronous: the counts are valid once the stream has completed the work. Runs of
+ * one plan must not overlap in time (they share the plan's packed copy).
+ * Errors: DNA_ERR_INVALID_ARG (NULL, wrong device), DNA_ERR_CUDA, DNA_ERR_NOMEM.
+ */
+int dna_batch_run(dna_batch *batch, dna_stream_t stream, uint64_t *out_counts);
+
+/* dna_batch_info -- the plan the batch runs with. */
+typedef struct {
+    uint32_t chunk_bases;      /* chunk length */
+    uint32_t warps_per_cta;
+    uint32_t grid;             /* persistent blocks */
+    uint32_t groups_per_task;  /* chunk groups (one chunk per lane) per ticket */
+    uint32_t n_fast;           /* automata in the persistent kernel */
+    uint32_t n_slow;           /* automata scanned with dna_scan */
+    uint64_t n_chunks;
+    uint64_t packed_tiles;     /* 512-base tiles of the packed copy */
+    uint32_t max_states;       /* largest automaton in the persistent kernel */
+} dna_batch_info_t;
+
+int dna_batch_info(const dna_batch *batch, dna_batch_info_t *out);
+
+/* dna_batch_free -- releases a plan (NULL is ignored). No run of it may be in flight. */
+void dna_batch_free(dna_batch *batch);
+
+/*
+ * dna_scan_batch -- one-shot form: dna_batch_create (default options), dna_batch_run,
+ * then dna_batch_free once the stream has finished the work. Arguments as above. The
+ * call returns after the counts are complete (it synchronises 'stream').
+ * Errors: as dna_batch_create and dna_batch_run.
  */
 int dna_scan_batch(const dna_dfa *const *dfas, uint32_t n_dfas,
                    const uint8_t *const *seqs, const uint64_t *lens, uint32_t n_seqs,
@@ -233,6 +301,12 @@ typedef struct {
     double   scan_kernel_ms;    /* summed duration of the chunk-scan kernel */
     uint64_t scan_kernel_calls;
     uint64_t kernel_launches;   /* all kernels launched by the library */
+    double   emit_kernel_ms;    /* position extraction kernel */
+    uint64_t emit_kernel_calls;
+    double   batch_kernel_ms;   /* batched scan kernel (dna_batch_run / dna_scan_batch) */
+    uint64_t batch_kernel_calls;
+    double   ingest_kernel_ms;  /* batched ingest (2-bit packing) kernel */
+    uint64_t ingest_kernel_calls;
 } dna_profile_t;
 
 void dna_profile_enable(int enable);

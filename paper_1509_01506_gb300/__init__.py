@@ -24,6 +24,7 @@ PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE = 0, 1, 2, 3
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
     "dna_scan_count_static", "dna_scan_host",
+    "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
     "dna_status_string", "dna_compile_regex", "dna_compile_kmers", "dna_free_host",
     "dna_profile_enable", "dna_profile_read",
 ]
@@ -50,7 +51,23 @@ class _Plan(ctypes.Structure):
 
 class _Profile(ctypes.Structure):
     _fields_ = [("scan_kernel_ms", ctypes.c_double), ("scan_kernel_calls", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64),
+                ("emit_kernel_ms", ctypes.c_double), ("emit_kernel_calls", ctypes.c_uint64),
+                ("batch_kernel_ms", ctypes.c_double), ("batch_kernel_calls", ctypes.c_uint64),
+                ("ingest_kernel_ms", ctypes.c_double), ("ingest_kernel_calls", ctypes.c_uint64)]
+
+
+class _BatchOpts(ctypes.Structure):
+    _fields_ = [("chunk_bases", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
+                ("autotune", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("chunk_bases", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("groups_per_task", ctypes.c_uint32),
+                ("n_fast", ctypes.c_uint32), ("n_slow", ctypes.c_uint32),
+                ("n_chunks", ctypes.c_uint64), ("packed_tiles", ctypes.c_uint64),
+                ("max_states", ctypes.c_uint32)]
 
 
 def build(force: bool = False) -> str:
@@ -89,6 +106,14 @@ def lib():
         L.dna_scan_count_static.restype = i32
         L.dna_scan_host.argtypes = [p, p, u64, p, p, p, u64]
         L.dna_scan_host.restype = i32
+        L.dna_batch_create.argtypes = [p, u32, p, p, u32, ctypes.POINTER(_BatchOpts), p, ctypes.POINTER(p)]
+        L.dna_batch_create.restype = i32
+        L.dna_batch_run.argtypes = [p, p, p]
+        L.dna_batch_run.restype = i32
+        L.dna_batch_info.argtypes = [p, ctypes.POINTER(_BatchInfo)]
+        L.dna_batch_info.restype = i32
+        L.dna_batch_free.argtypes = [p]
+        L.dna_batch_free.restype = None
         L.dna_scan_batch.argtypes = [p, u32, p, p, u32, p, p]
         L.dna_scan_batch.restype = i32
         L.dna_status_string.argtypes = [i32]
@@ -325,20 +350,92 @@ def scan_host(dfa: Dfa, seq, positions: bool = False, capacity: int | None = Non
     return c, (out_positions[:c] if positions else None)
 
 
-def scan_batch(dfas, seqs, stream=None, out=None):
-    """dna_scan_batch: counts [n_seqs, n_dfas] (int64 tensor) for CUDA uint8 tensors."""
+def _batch_arrays(dfas, seqs, lens=None):
+    """ctypes arrays of handles, device pointers and lengths. 'seqs' holds CUDA uint8
+    tensors, or raw device pointers when 'lens' is given."""
+    n_d, n_s = len(dfas), len(seqs)
+    hs = (ctypes.c_void_p * n_d)(*[d.handle for d in dfas])
+    if lens is None:
+        ptrs = (ctypes.c_void_p * n_s)(*[t.data_ptr() for t in seqs])
+        ls = (ctypes.c_uint64 * n_s)(*[t.numel() for t in seqs])
+    else:
+        ptrs = (ctypes.c_void_p * n_s)(*[int(x) for x in seqs])
+        ls = (ctypes.c_uint64 * n_s)(*[int(x) for x in lens])
+    return hs, ptrs, ls
+
+
+def scan_batch(dfas, seqs, stream=None, out=None, lens=None):
+    """dna_scan_batch: counts [n_seqs, n_dfas] (int64 tensor) of CUDA uint8 tensors (or
+    raw device pointers with 'lens'). Synchronous (one-shot plan)."""
     import torch
     n_d, n_s = len(dfas), len(seqs)
-    dev = seqs[0].device
-    hs = (ctypes.c_void_p * n_d)(*[d.handle for d in dfas])
-    ptrs = (ctypes.c_void_p * n_s)(*[s.data_ptr() for s in seqs])
-    lens = (ctypes.c_uint64 * n_s)(*[s.numel() for s in seqs])
+    hs, ptrs, ls = _batch_arrays(dfas, seqs, lens)
     if out is None:
-        out = torch.empty((n_s, n_d), dtype=torch.int64, device=dev)
+        out = torch.empty((n_s, n_d), dtype=torch.int64, device="cuda")
     _check(lib().dna_scan_batch(ctypes.cast(hs, ctypes.c_void_p), n_d,
-                                ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(lens, ctypes.c_void_p),
+                                ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(ls, ctypes.c_void_p),
                                 n_s, _stream_handle(stream), out.data_ptr()), "dna_scan_batch")
     return out
+
+
+@dataclass
+class BatchInfo:
+    chunk_bases: int
+    warps_per_cta: int
+    grid: int
+    groups_per_task: int
+    n_fast: int
+    n_slow: int
+    n_chunks: int
+    packed_tiles: int
+    max_states: int
+
+
+class Batch:
+    """A reusable batched-scan plan (dna_batch_create / dna_batch_run / dna_batch_free).
+    The sequences (CUDA uint8 tensors, or device pointers with 'lens') must stay
+    allocated while the plan exists; the automata must outlive it too."""
+
+    def __init__(self, dfas, seqs, lens=None, chunk_bases: int = 0, warps_per_cta: int = 0,
+                 autotune: bool = False, use_graph: bool = False, stream=None):
+        self._dfas = list(dfas)
+        self._seqs = list(seqs)
+        self.n_dfas, self.n_seqs = len(self._dfas), len(self._seqs)
+        hs, ptrs, ls = _batch_arrays(self._dfas, self._seqs, lens)
+        opts = _BatchOpts(chunk_bases, warps_per_cta, 1 if autotune else 0, 1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        _check(lib().dna_batch_create(ctypes.cast(hs, ctypes.c_void_p), self.n_dfas,
+                                      ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(ls, ctypes.c_void_p),
+                                      self.n_seqs, ctypes.byref(opts), _stream_handle(stream),
+                                      ctypes.byref(h)), "dna_batch_create")
+        self._h = h
+
+    def run(self, out=None, stream=None):
+        """Queues the batch; returns the [n_seqs, n_dfas] int64 counts tensor."""
+        import torch
+        if not self._h:
+            raise ValueError("batch was freed")
+        if out is None:
+            out = torch.empty((self.n_seqs, self.n_dfas), dtype=torch.int64, device="cuda")
+        _check(lib().dna_batch_run(self._h, _stream_handle(stream), out.data_ptr()), "dna_batch_run")
+        return out
+
+    def info(self) -> BatchInfo:
+        i = _BatchInfo()
+        _check(lib().dna_batch_info(self._h, ctypes.byref(i)), "dna_batch_info")
+        return BatchInfo(i.chunk_bases, i.warps_per_cta, i.grid, i.groups_per_task, i.n_fast,
+                         i.n_slow, i.n_chunks, i.packed_tiles, i.max_states)
+
+    def free(self):
+        if self._h:
+            lib().dna_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def profile_enable(on: bool = True):
@@ -348,5 +445,4 @@ def profile_enable(on: bool = True):
 def profile_read(reset: bool = False) -> dict:
     pr = _Profile()
     _check(lib().dna_profile_read(ctypes.byref(pr), 1 if reset else 0), "dna_profile_read")
-    return {"scan_kernel_ms": pr.scan_kernel_ms, "scan_kernel_calls": pr.scan_kernel_calls,
-            "kernel_launches": pr.kernel_launches}
+    return {k: getattr(pr, k) for k, _ in _Profile._fields_}

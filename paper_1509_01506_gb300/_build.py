@@ -8,9 +8,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIBDIR = os.path.join(HERE, "_lib")
 LIBPATH = os.path.join(LIBDIR, "libdnadfa.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("dna_scan.cu", "dna_compile.cpp")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "dna_internal.h"),
-                  os.path.join(ROOT, "include", "dna_dfa.h")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("dna_scan.cu", "dna_batch.cu", "dna_compile.cpp")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("dna_internal.h", "dna_runtime.h", "dna_device.cuh")] + \
+    [os.path.join(ROOT, "include", "dna_dfa.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -29,16 +29,31 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles each source to an object in parallel (one nvcc per file), then links."""
     if not force and up_to_date():
         return LIBPATH
+    import concurrent.futures as cf
     os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIBPATH + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", ARCH, "-lineinfo",
-           "--threads", "2", "-o", tmp] + SOURCES
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIBPATH)
+    tag = f"{os.getpid()}"
+    objs = [os.path.join(LIBDIR, os.path.basename(src) + f".{tag}.o") for src in SOURCES]
+
+    def compile_one(src, obj):
+        cmd = [nvcc(), "-O3", "-std=c++17", "-Xcompiler", "-fPIC", ARCH, "-lineinfo", "-c", src, "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        subprocess.check_call(cmd)
+
+    try:
+        with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
+            for f in [ex.submit(compile_one, s, o) for s, o in zip(SOURCES, objs)]:
+                f.result()
+        tmp = LIBPATH + f".{tag}.tmp"
+        subprocess.check_call([nvcc(), "-shared", ARCH, "-o", tmp] + objs)
+        os.replace(tmp, LIBPATH)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIBPATH
 
 

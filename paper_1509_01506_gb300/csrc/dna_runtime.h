@@ -1,0 +1,69 @@
+// dna_runtime.h -- host-side internals shared by the library's CUDA translation units
+// (dna_scan.cu and dna_batch.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/dna_dfa.h"
+
+// A loaded automaton: its tables on the device it was loaded on, plus the host-side
+// analysis that the scans plan with.
+struct dna_dfa {
+    uint32_t n_states = 0;
+    int device = 0;
+    int definite_depth = -1;
+    uint32_t lookback = 0;
+    uint32_t placement = DNA_PLACE_AUTO;
+    uint32_t accept0 = 0;
+    uint32_t reset_entry = 0;
+    uint32_t *d_one = nullptr;    // [n_states][4] one-symbol entries, code order A, C, T, G
+    uint32_t *d_pair = nullptr;   // [n_states][16] compact pair entries (small automata)
+    // resident blocks per SM of each scan kernel variant with this automaton's shared
+    // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
+    std::atomic<int> per_sm[3][4][2] = {};
+};
+
+namespace dnalib {
+
+int cuda_status(cudaError_t e);
+
+struct DeviceProps {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+DeviceProps device_props(int dev);
+
+// Raises a kernel's dynamic shared-memory limit to 'bytes' once per (kernel, device).
+int ensure_smem_optin(const void *fn, int device, size_t bytes);
+
+size_t align_up(size_t x, size_t a);
+
+// Counts kernels launched by the library (reported by dna_profile_read).
+void record_launch(int n = 1);
+
+// The single-sequence scan behind dna_scan / dna_scan_planned.
+int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
+              uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov);
+
+// Kernel timing: prof_begin records an event on the stream when profiling is enabled
+// (otherwise returns an empty token); prof_end records the closing event.
+enum ProfKernel { PROF_SCAN = 0, PROF_EMIT = 1, PROF_BATCH = 2, PROF_INGEST = 3, PROF_N = 4 };
+struct ProfToken {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+ProfToken prof_begin(cudaStream_t s);
+void prof_end(ProfToken t, cudaStream_t s, int which);
+void profile_set(int on);
+void profile_collect(dna_profile_t *out, int reset);
+
+}  // namespace dnalib
+
+#define DNA_CUDA(call)                                           \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return dnalib::cuda_status(_e);   \
+    } while (0)

@@ -43,68 +43,24 @@
 
 #include "../../include/dna_dfa.h"
 #include "dna_internal.h"
+#include "dna_device.cuh"
+#include "dna_runtime.h"
+
+using namespace dnalib;
 
 namespace {
 
 // ------------------------------------------------------------------ constants
 
-constexpr int kTile = 128;          // bytes per chunk row staged per step
 constexpr int kStages = 1;          // one stage per warp: rows are copied to registers first
 constexpr int kStageBytes = 32 * kTile;
 constexpr int kStashCap = 8;        // hit-row records kept per chunk before a rescan
-constexpr int kPairRowBytes = 16 * 32 * 4;  // 16 symbol pairs x 32 lanes x 4 bytes
 constexpr uint32_t kMaxLookback = 64;
 constexpr uint32_t kMaxStates = 1u << 24;
 constexpr uint32_t kDefaultPrefetch = 0;  // tiles of L2 prefetch ahead of the stage
 
 enum Mode { MODE_PAIR = 0, MODE_ONE_SMEM = 1, MODE_ONE_GLOBAL = 2 };
 
-std::atomic<uint64_t> g_launches{0};
-std::atomic<int> g_profile{0};
-std::mutex g_prof_mu;
-struct ProfRec { cudaEvent_t a, b; };
-std::vector<ProfRec> g_prof_pending;
-std::vector<ProfRec> g_prof_free;   // recorded pairs are reused
-double g_prof_ms = 0.0;
-uint64_t g_prof_calls = 0;
-
-// ----------------------------------------------------------- device helpers
-
-// Byte -> code: code = (byte >> 1) & 3 gives A=0, C=1, T=2, G=3 for both cases; a byte
-// is a base iff (byte | 0x20) equals the lowercase letter of its code.
-__device__ __forceinline__ bool byte_is_base(uint32_t b) {
-    uint32_t code = (b >> 1) & 3u;
-    uint32_t expect = (0x67746361u >> (code << 3)) & 0xFFu;  // 'a','c','t','g'
-    return (b | 0x20u) == expect;
-}
-
-__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
-                 :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-template <int OFF>
-__device__ __forceinline__ void cp_async16_full(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0+%2], [%1], 16;\n"
-                 :: "r"(dst), "l"(src), "n"(OFF) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" :: "n"(N) : "memory"); }
-
-// One-symbol entry: next state in bits 0..30, bit 31 = next state accepts.
-struct OneTable {
-    const uint32_t *t;      // [n_states][4] in code order (A, C, T, G)
-    uint32_t reset_entry;   // entry taken on a reset byte: state 0 (+ its accept bit)
-    __device__ __forceinline__ uint32_t step(uint32_t q, uint32_t b) const {
-        return byte_is_base(b) ? t[q * 4u + ((b >> 1) & 3u)] : reset_entry;
-    }
-};
 
 // -------------------------------------------------------------- scan kernel
 
@@ -166,35 +122,6 @@ __device__ __forceinline__ void record_hit_row(uint32_t *stash, uint32_t &nrec, 
     ++nrec;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
-}
-
-__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
-    uint32_t d;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
-    uint32_t d;
-    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-// Pair-table entry layout (lane l's copy): bits 0..17 = shared address of the next
-// state's row for lane l (row base 2048-aligned, so bits 7..10 are zero), bits 27..28 =
-// accepting steps in the pair. The two codes of a pair enter at bits 7..10.
-constexpr uint32_t kPairMuxMask = 0x78000780u;
-constexpr int kCountShift = 27;
-
-// Bitwise select with the pair-table mask: bits of b where kPairMuxMask is set, bits of a
-// elsewhere. Written as one lop3 (lut 0xD8 = (a & ~c) | (b & c)); the C++ form of the
-// same select compiles to two logic instructions.
-__device__ __forceinline__ uint32_t mux_pair(uint32_t a, uint32_t b) {
-    uint32_t d;
-    asm("lop3.b32 %0, %1, %2, %3, 0xD8;" : "=r"(d) : "r"(a), "r"(b), "n"(kPairMuxMask));
-    return d;
-}
-
 // After a chunk's speculative run was repaired at its converging point (the true start
 // and the speculated start met within the chunk's first row), the hit-row records of the
 // speculative run are made those of the true run: row 0 is re-walked from the true start,
@@ -220,38 +147,6 @@ __device__ __forceinline__ void fix_hit_rows(uint32_t *stash, uint32_t &nrec, ui
             stash[0] = 0; stash[1] = q_true; stash[2] = 0;
         }
         ++nrec;   // beyond the capacity: the extraction pass rescans the chunk
-    }
-}
-
-__device__ __forceinline__ uint32_t one_step(const uint32_t *one, uint32_t reset_entry, uint32_t q,
-                                             uint32_t b) {
-    return byte_is_base(b) ? one[q * 4u + ((b >> 1) & 3u)] : reset_entry;
-}
-
-// Walks aligned offsets [from, to) of the sequence in 128-byte blocks: each block is
-// fetched with eight independent 16-byte loads (a 16-byte granule is loaded only if it
-// starts before 'hi', so no load leaves the sequence's last page), then f(offset, byte)
-// is called in order. f returns false to stop the walk.
-template <class F>
-__device__ __forceinline__ void walk_range(const uint8_t *abase, uint64_t from, uint64_t to, uint64_t hi,
-                                           F &&f) {
-    for (uint64_t blk = from & ~(uint64_t)(kTile - 1); blk < to; blk += kTile) {
-        uint4 v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint64_t g = blk + 16u * j;
-            v[j] = g < hi ? *reinterpret_cast<const uint4 *>(abase + g) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int k4 = 0; k4 < 32; ++k4) {
-            const uint4 &vv = v[k4 >> 2];
-            const uint32_t word = (k4 & 3) == 0 ? vv.x : (k4 & 3) == 1 ? vv.y : (k4 & 3) == 2 ? vv.z : vv.w;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint64_t o = blk + 4u * k4 + i;
-                if (o >= from && o < to && !f(o, (word >> (8 * i)) & 0xFFu)) return;
-            }
-        }
     }
 }
 
@@ -889,7 +784,11 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
 
 __global__ void write_zero_kernel(uint64_t *out) { *out = 0; }
 
+}  // namespace
+
 // ------------------------------------------------------------------ host side
+
+namespace dnalib {
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DNA_OK;
@@ -899,17 +798,6 @@ int cuda_status(cudaError_t e) {
         return DNA_ERR_NO_DEVICE;
     return DNA_ERR_CUDA;
 }
-
-#define DNA_CUDA(call)                                   \
-    do {                                                 \
-        cudaError_t _e = (call);                         \
-        if (_e != cudaSuccess) return cuda_status(_e);   \
-    } while (0)
-
-struct DeviceProps {
-    int sms = 0;
-    size_t smem_optin = 0;
-};
 
 DeviceProps device_props(int dev) {
     static std::mutex mu;
@@ -924,6 +812,91 @@ DeviceProps device_props(int dev) {
     }
     return cache[dev];
 }
+
+// Raises a kernel's dynamic shared-memory limit to 'bytes' once per (kernel, device).
+int ensure_smem_optin(const void *fn, int device, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == fn && d.second == device) return DNA_OK;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    done.emplace_back(fn, device);
+    return DNA_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::atomic<uint64_t> g_launches{0};
+void record_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Kernel timing for dna_profile_*: an event pair around each timed launch, resolved
+// (and recycled) when the counters are read.
+static std::atomic<int> g_profile{0};
+static std::mutex g_prof_mu;
+struct ProfRec { cudaEvent_t a, b; int which; };
+static std::vector<ProfRec> g_prof_pending;
+static std::vector<ProfRec> g_prof_free;
+static double g_prof_ms[PROF_N] = {};
+static uint64_t g_prof_calls[PROF_N] = {};
+
+ProfToken prof_begin(cudaStream_t s) {
+    ProfToken t;
+    if (g_profile.load(std::memory_order_relaxed) == 0) return t;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_free.empty()) {
+            t.a = g_prof_free.back().a; t.b = g_prof_free.back().b;
+            g_prof_free.pop_back();
+        }
+    }
+    if (!t.a && (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess)) {
+        t.a = t.b = nullptr;
+        return t;
+    }
+    cudaEventRecord(t.a, s);
+    return t;
+}
+
+void prof_end(ProfToken t, cudaStream_t s, int which) {
+    if (!t.a) return;
+    cudaEventRecord(t.b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back({t.a, t.b, which});
+}
+
+void profile_set(int on) { g_profile.store(on ? 1 : 0); }
+
+void profile_collect(dna_profile_t *out, int reset) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_prof_ms[r.which] += ms;
+            ++g_prof_calls[r.which];
+        }
+        g_prof_free.push_back(r);
+    }
+    g_prof_pending.clear();
+    out->scan_kernel_ms = g_prof_ms[PROF_SCAN];
+    out->scan_kernel_calls = g_prof_calls[PROF_SCAN];
+    out->kernel_launches = g_launches.load();
+    out->emit_kernel_ms = g_prof_ms[PROF_EMIT];
+    out->emit_kernel_calls = g_prof_calls[PROF_EMIT];
+    out->batch_kernel_ms = g_prof_ms[PROF_BATCH];
+    out->batch_kernel_calls = g_prof_calls[PROF_BATCH];
+    out->ingest_kernel_ms = g_prof_ms[PROF_INGEST];
+    out->ingest_kernel_calls = g_prof_calls[PROF_INGEST];
+    if (reset) {
+        for (int k = 0; k < PROF_N; ++k) { g_prof_ms[k] = 0; g_prof_calls[k] = 0; }
+        g_launches.store(0);
+    }
+}
+
+}  // namespace dnalib
+
+namespace {
 
 // Dynamic shared memory of the scan kernel (the launch argument).
 size_t scan_smem_bytes(int mode, int warps, uint32_t n_states) {
@@ -953,25 +926,6 @@ ScanFn scan_fn(int mode, int warps, bool pos) {
     return nullptr;
 }
 
-}  // namespace
-
-struct dna_dfa {
-    uint32_t n_states = 0;
-    int device = 0;
-    int definite_depth = -1;
-    uint32_t lookback = 0;
-    uint32_t placement = DNA_PLACE_AUTO;
-    uint32_t accept0 = 0;
-    uint32_t reset_entry = 0;
-    uint32_t *d_one = nullptr;
-    uint32_t *d_pair = nullptr;
-    // resident blocks per SM of each scan kernel variant with this automaton's shared
-    // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
-    std::atomic<int> per_sm[3][4][2] = {};
-};
-
-namespace {
-
 // code order (A, C, T, G) -> table column (A, C, G, T)
 constexpr int kColOfCode[4] = {0, 1, 3, 2};
 
@@ -990,19 +944,6 @@ struct Plan {
     size_t smem;
     int grid;
 };
-
-// Raises a kernel's dynamic shared-memory limit to 'bytes' once per (kernel, device).
-int ensure_smem_optin(const void *fn, int device, size_t bytes) {
-    static std::mutex mu;
-    static std::vector<std::pair<const void *, int>> done;
-    std::lock_guard<std::mutex> lk(mu);
-    for (auto &d : done)
-        if (d.first == fn && d.second == device) return DNA_OK;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return cuda_status(e);
-    done.emplace_back(fn, device);
-    return DNA_OK;
-}
 
 int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Plan &pl) {
     DeviceProps pr = device_props(d->device);
@@ -1068,7 +1009,6 @@ struct Scratch {
     size_t bytes;
 };
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t pending_cap,
            uint32_t div_cap, uint8_t *base) {
@@ -1089,7 +1029,9 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
     s.bytes = off;
 }
 
-void record_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace
+
+namespace dnalib {
 
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov) {
@@ -1133,29 +1075,13 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
     sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
 
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    const bool prof = g_profile.load(std::memory_order_relaxed) != 0;
-    if (prof && e == cudaSuccess) {
-        {
-            std::lock_guard<std::mutex> lk(g_prof_mu);
-            if (!g_prof_free.empty()) {
-                ev0 = g_prof_free.back().a; ev1 = g_prof_free.back().b;
-                g_prof_free.pop_back();
-            }
-        }
-        if (!ev0) { cudaEventCreate(&ev0); cudaEventCreate(&ev1); }
-        cudaEventRecord(ev0, stream);
-    }
+    const ProfToken tok = e == cudaSuccess ? prof_begin(stream) : ProfToken{};
     if (e == cudaSuccess) {
         scan_fn(pl.mode, pl.warps, pl.pos)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);
         e = cudaGetLastError();
         record_launch();
     }
-    if (prof && ev1) {
-        cudaEventRecord(ev1, stream);
-        std::lock_guard<std::mutex> lk(g_prof_mu);
-        g_prof_pending.push_back({ev0, ev1});
-    }
+    prof_end(tok, stream, PROF_SCAN);
     if (e == cudaSuccess && positions) {
         EmitParams ep;
         ep.abase = abase; ep.lo = shift; ep.hi = total; ep.seg_bytes = pl.seg_bytes; ep.nseg = pl.nseg;
@@ -1170,7 +1096,11 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         // the extraction kernel's static shared memory is about 10 KB; 16 KB is reserved
         int rc2 = ensure_smem_optin((const void *)emit_kernel, d->device, (optin ? optin : 232448) - 16384);
         if (rc2) e = cudaErrorInvalidValue;
-        else emit_kernel<<<pl.grid, cpb, esmem, stream>>>(ep, tab5_smem);
+        else {
+            const ProfToken et = prof_begin(stream);
+            emit_kernel<<<pl.grid, cpb, esmem, stream>>>(ep, tab5_smem);
+            prof_end(et, stream, PROF_EMIT);
+        }
         e = cudaGetLastError();
         record_launch();
     }
@@ -1179,7 +1109,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     return cuda_status(e);
 }
 
-}  // namespace
+}  // namespace dnalib
 
 // ====================================================================== C ABI
 
@@ -1393,19 +1323,6 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     return cuda_status(cudaGetLastError());
 }
 
-extern "C" int dna_scan_batch(const dna_dfa *const *dfas, uint32_t n_dfas, const uint8_t *const *seqs,
-                              const uint64_t *lens, uint32_t n_seqs, dna_stream_t stream,
-                              uint64_t *out_counts) {
-    if (!dfas || !seqs || !lens || !out_counts || n_dfas == 0 || n_seqs == 0) return DNA_ERR_INVALID_ARG;
-    for (uint32_t s = 0; s < n_seqs; ++s)
-        for (uint32_t k = 0; k < n_dfas; ++k) {
-            int rc = scan_impl(dfas[k], seqs[s], lens[s], (cudaStream_t)stream,
-                               out_counts + (uint64_t)s * n_dfas + k, nullptr, 0, nullptr);
-            if (rc) return rc;
-        }
-    return DNA_OK;
-}
-
 extern "C" const char *dna_status_string(int status) {
     switch (status) {
         case DNA_OK: return "ok";
@@ -1421,27 +1338,10 @@ extern "C" const char *dna_status_string(int status) {
     }
 }
 
-extern "C" void dna_profile_enable(int enable) { g_profile.store(enable ? 1 : 0); }
+extern "C" void dna_profile_enable(int enable) { dnalib::profile_set(enable); }
 
 extern "C" int dna_profile_read(dna_profile_t *out, int reset) {
     if (!out) return DNA_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(g_prof_mu);
-    for (auto &r : g_prof_pending) {
-        float ms = 0;
-        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-            g_prof_ms += ms;
-            ++g_prof_calls;
-        }
-        g_prof_free.push_back(r);
-    }
-    g_prof_pending.clear();
-    out->scan_kernel_ms = g_prof_ms;
-    out->scan_kernel_calls = g_prof_calls;
-    out->kernel_launches = g_launches.load();
-    if (reset) {
-        g_prof_ms = 0;
-        g_prof_calls = 0;
-        g_launches.store(0);
-    }
+    dnalib::profile_collect(out, reset);
     return DNA_OK;
 }

@@ -183,11 +183,23 @@ def plain_large(n: int = 3435973837, kmers: int = 1000) -> tuple[np.ndarray, lis
 
 
 def batched(n_seqs: int = 4096, n_dfas: int = 64, lo: int = 1024, hi: int = 16 * MiB,
-            seed: int = 3) -> tuple[np.ndarray, np.ndarray, list[str]]:
+            seed: int = 3, n_states=None, state_range: tuple[int, int] = (5, 60)
+            ) -> tuple[np.ndarray, np.ndarray, list[str]]:
     """Sequences with log-uniform lengths in [lo, hi] (i.i.d. ACGT, one contiguous
-    buffer) and random motif regexes. Returns (buffer, offsets[n_seqs+1], regexes)."""
+    buffer) and random motif regexes. Returns (buffer, offsets[n_seqs+1], regexes).
+    With 'n_states' (a callable giving a pattern's minimal state count, supplied by the
+    caller), motifs are drawn until n_dfas fall inside state_range; without it the
+    first n_dfas motifs are returned."""
     lens = log_uniform_lengths(seed, n_seqs, lo, hi)
     offs = np.zeros(n_seqs + 1, dtype=np.int64)
     offs[1:] = np.cumsum(lens)
     buf = uniform(seed, int(offs[-1]))
-    return buf, offs, random_regexes(seed, n_dfas)
+    if n_states is None:
+        return buf, offs, random_regexes(seed, n_dfas)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < n_dfas:
+        r = random_motif_regex(rng)
+        if state_range[0] <= n_states(r) <= state_range[1]:
+            out.append(r)
+    return buf, offs, out
