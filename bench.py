@@ -68,13 +68,13 @@ def load_peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the scan kernel's source: the device code of dna_scan.cu up to the
-    extraction section (helpers, scan kernel, last-block join). Host code below it does
-    not change the kernel's DRAM traffic."""
-    with open(os.path.join(ROOT, "paper_1509_01506_gb300/csrc/dna_scan.cu"), "rb") as fh:
-        src = fh.read()
-    end = src.find(b"// ------------------------------------------------------------ extraction")
-    return hashlib.sha256(src[:end if end > 0 else len(src)]).hexdigest()[:16]
+    """Hash of the scan kernel's source: its template and join (scan_kernel.cuh) and the
+    device helpers it uses (dna_device.cuh). Host code does not change its traffic."""
+    h = hashlib.sha256()
+    for f in ("scan_kernel.cuh", "dna_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1509_01506_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic():

@@ -45,567 +45,11 @@
 #include "dna_internal.h"
 #include "dna_device.cuh"
 #include "dna_runtime.h"
+#include "scan_kernel.cuh"
 
 using namespace dnalib;
 
 namespace {
-
-// ------------------------------------------------------------------ constants
-
-constexpr int kStages = 1;          // one stage per warp: rows are copied to registers first
-constexpr int kStageBytes = 32 * kTile;
-constexpr int kStashCap = 8;        // hit-row records kept per chunk before a rescan
-constexpr uint32_t kMaxLookback = 64;
-constexpr uint32_t kMaxStates = 1u << 24;
-constexpr uint32_t kDefaultPrefetch = 0;  // tiles of L2 prefetch ahead of the stage
-
-enum Mode { MODE_PAIR = 0, MODE_ONE_SMEM = 1, MODE_ONE_GLOBAL = 2 };
-
-
-// -------------------------------------------------------------- scan kernel
-
-struct ScanParams {
-    const uint8_t *abase;   // 16-byte aligned base; sequence byte j is abase[lo + j]
-    uint64_t lo, hi;        // valid aligned offsets [lo, hi)
-    uint64_t seg_bytes;     // chunk length (multiple of kTile)
-    uint64_t nseg;
-    uint32_t lookback;
-    uint32_t n_states;
-    uint32_t reset_entry;
-    const uint32_t *one;    // global one-symbol table
-    const uint32_t *pair;   // global compact pair table: next | count << 24
-    uint32_t *spec_start;   // [nseg] speculated start state
-    uint32_t *last_state;   // [nseg] state after the chunk (from the speculated start)
-    uint32_t *count;        // [nseg] accepting steps (from the speculated start)
-    uint32_t *stash;        // [nseg][kStashCap][3] hit rows {tile, start state, count before}, or null
-    uint32_t prefetch_tiles; // L2 prefetch distance in tiles (0 = off)
-    uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
-    uint8_t *flags;         // [nseg] 1 = extraction must rescan the chunk from its true start
-    uint32_t *ctrl;         // [4] zeroed before launch: finish ticket, pending, diverged, 0
-    uint32_t *pending;      // chunks the last block must repair (first chunk of each block,
-    uint32_t pending_cap;   //   and chunks whose 16-byte repair did not converge)
-    uint32_t *pending_a;    // [pending_cap] snapshot of each pending chunk's true start
-    uint32_t *div_list;     // [div_cap] chunks whose last state changed in a repair
-    uint32_t div_cap;
-    unsigned long long *cta_sum;   // [grid] count of each block's chunks
-    unsigned long long *cta_off;   // [grid] exclusive prefix of cta_sum (for extraction)
-    uint64_t *out_count;
-    // 1, 2^16, 2^5, 2^28 passed at run time so the compiler keeps the multiplies that
-    // use them (adds and shifts) on the FMA pipe instead of turning them into ALU ops
-    uint32_t k1, k16, k5, k28;
-    // lowercase letters selected by the codes (a, c at bytes 0, 2; t, g at bytes 4, 6),
-    // passed at run time so that they stay in registers across the unrolled row loop
-    uint32_t lut_lo, lut_hi;
-};
-
-// Per-byte walk over a full 128-byte row held in registers (rows with reset bytes).
-__device__ __forceinline__ uint32_t row_bytes_reg(const OneTable &T, uint32_t q, const uint32_t (&w)[32],
-                                                  uint32_t &cnt) {
-#pragma unroll
-    for (int k = 0; k < kTile; ++k) {
-        uint32_t e = T.step(q, (w[k >> 2] >> (8 * (k & 3))) & 0xFFu);
-        q = e & 0x7FFFFFFFu;
-        cnt += e >> 31;
-    }
-    return q;
-}
-
-// Records a row that contains accepting steps: the emit pass re-walks it from 'q_row'
-// and writes its positions starting at the chunk's offset + 'cnt_before'.
-__device__ __forceinline__ void record_hit_row(uint32_t *stash, uint32_t &nrec, uint32_t t,
-                                               uint32_t q_row, uint32_t cnt_before) {
-    if (nrec < (uint32_t)kStashCap) {
-        stash[nrec * 3] = t;
-        stash[nrec * 3 + 1] = q_row;
-        stash[nrec * 3 + 2] = cnt_before;
-    }
-    ++nrec;
-}
-
-// After a chunk's speculative run was repaired at its converging point (the true start
-// and the speculated start met within the chunk's first row), the hit-row records of the
-// speculative run are made those of the true run: row 0 is re-walked from the true start,
-// later rows keep their start states (the runs coincide there) and shift their count
-// offsets by delta = true prefix count - speculative prefix count. 'pa' is the true run's
-// count over the prefix; if the true prefix has accepting steps but row 0 had no record,
-// a record for row 0 is inserted in front.
-__device__ __forceinline__ void fix_hit_rows(uint32_t *stash, uint32_t &nrec, uint32_t q_true,
-                                             uint32_t delta, uint32_t pa) {
-    const uint32_t n = nrec < (uint32_t)kStashCap ? nrec : (uint32_t)kStashCap;
-    bool row0 = false;
-    for (uint32_t r = 0; r < n; ++r) {
-        if (stash[3 * r] == 0) { stash[3 * r + 1] = q_true; row0 = true; }
-        else stash[3 * r + 2] += delta;
-    }
-    if (!row0 && pa > 0) {
-        if (nrec < (uint32_t)kStashCap) {
-            for (uint32_t r = n; r > 0; --r) {
-                stash[3 * r] = stash[3 * (r - 1)];
-                stash[3 * r + 1] = stash[3 * (r - 1) + 1];
-                stash[3 * r + 2] = stash[3 * (r - 1) + 2];
-            }
-            stash[0] = 0; stash[1] = q_true; stash[2] = 0;
-        }
-        ++nrec;   // beyond the capacity: the extraction pass rescans the chunk
-    }
-}
-
-// Per-byte walk over aligned offsets [from, to) read from global memory: rows with a
-// reset byte, the first row of an unaligned sequence and the last row of the last chunk.
-__device__ __forceinline__ uint32_t row_bytes_global(const OneTable &T, uint32_t q, const uint8_t *abase,
-                                                     uint64_t from, uint64_t to, uint64_t hi, uint32_t &cnt) {
-    walk_range(abase, from, to, hi, [&](uint64_t, uint32_t byte) {
-        const uint32_t e = T.step(q, byte);
-        q = e & 0x7FFFFFFFu;
-        cnt += e >> 31;
-        return true;
-    });
-    return q;
-}
-
-// Converging-point repair (Sec. III-B.3, Alg. 1) of chunk c from global memory: the true
-// start 'a' and the start 's' that the chunk's current results assume run in lockstep
-// until their states meet; from there on both runs coincide, so the true count is the
-// true prefix count + (current count - assumed prefix count) and the last state is
-// unchanged. A run that never meets gives the chunk's true count and last state directly.
-// Hit-row records are fixed when the runs meet inside row 0; otherwise the chunk is
-// flagged for a rescan by the extraction pass. Requires the chunk's current results
-// (count, last state, records) to be those of the run from 's'.
-struct Repair { uint32_t count, last; uint8_t flag; };
-
-__device__ Repair repair_chunk(const ScanParams &p, uint64_t c, uint32_t a, uint32_t s) {
-    const uint64_t b = c * p.seg_bytes;
-    const uint64_t from = b > p.lo ? b : p.lo;
-    const uint64_t to = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
-    uint32_t qa = a, qs = s, ca = 0, cs = 0;
-    uint64_t met_at = ~0ull;
-    walk_range(p.abase, from, to, p.hi, [&](uint64_t off, uint32_t byte) {
-        const uint32_t ea = one_step(p.one, p.reset_entry, qa, byte);
-        const uint32_t es = one_step(p.one, p.reset_entry, qs, byte);
-        qa = ea & 0x7FFFFFFFu; qs = es & 0x7FFFFFFFu;
-        ca += ea >> 31; cs += es >> 31;
-        if (qa == qs) { met_at = off; return false; }
-        return true;
-    });
-    Repair r;
-    if (met_at != ~0ull) {
-        r.count = p.count[c] - cs + ca;
-        r.last = p.last_state[c];
-        r.flag = 0;
-        if (p.stash) {
-            if (met_at < b + kTile) {
-                uint32_t nr = p.nrec[c];
-                fix_hit_rows(p.stash + c * (kStashCap * 3), nr, a, ca - cs, ca);
-                p.nrec[c] = nr;
-            } else {
-                r.flag = 1;
-            }
-        }
-    } else {
-        r.count = ca;
-        r.last = qa;
-        r.flag = 1;
-    }
-    return r;
-}
-
-// Makes chunk c's results those of the run from its true start a: count (and its block
-// sum), assumed start, last state, flags.
-__device__ __forceinline__ void apply_repair(const ScanParams &p, uint64_t c, uint32_t a,
-                                             const Repair &r, uint32_t chunks_per_block) {
-    const uint32_t old = p.count[c];
-    p.count[c] = r.count;
-    atomicAdd(&p.cta_sum[c / chunks_per_block], (unsigned long long)(long long)((int64_t)r.count - (int64_t)old));
-    p.spec_start[c] = a;
-    p.last_state[c] = r.last;
-    if (r.flag) p.flags[c] = 1;
-}
-
-// The join across blocks (Sec. III-A "binary reduction"), run by the last block to
-// finish: repairs the pending chunks in parallel (each from the last state of the chunk
-// before it, as it stood when the blocks finished), then walks forward from every chunk
-// whose last state changed until the chain agrees again, then writes the total count and
-// each block's output offset. Every chunk's (assumed start, count, last state) triple
-// stays consistent throughout.
-template <int THREADS>
-__device__ void finalize_block(const ScanParams &p) {
-    __shared__ unsigned long long wsum[THREADS / 32];
-    __shared__ unsigned long long carry;
-    const uint32_t tid = threadIdx.x;
-    const uint32_t cpb = THREADS;   // chunks per scan block
-    const uint32_t np = p.ctrl[1];
-    if (np <= p.pending_cap) {
-        for (uint32_t i = tid; i < np; i += THREADS) p.pending_a[i] = p.last_state[p.pending[i] - 1];
-        __syncthreads();
-        for (uint32_t i = tid; i < np; i += THREADS) {
-            const uint64_t c = p.pending[i];
-            const uint32_t a = p.pending_a[i];
-            const uint32_t s = p.spec_start[c];
-            if (a == s) continue;
-            const uint32_t old_last = p.last_state[c];
-            const Repair r = repair_chunk(p, c, a, s);
-            apply_repair(p, c, a, r, cpb);
-            if (r.last != old_last) {
-                const uint32_t k = atomicAdd(&p.ctrl[2], 1u);
-                if (k < p.div_cap) p.div_list[k] = (uint32_t)c;
-            }
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const uint32_t nd = p.ctrl[2];
-        if (np > p.pending_cap || nd > p.div_cap) {
-            // a list overflowed: check every chunk boundary in order
-            for (uint64_t c = 1; c < p.nseg; ++c) {
-                const uint32_t a = p.last_state[c - 1];
-                const uint32_t s = p.spec_start[c];
-                if (a == s) continue;
-                const Repair r = repair_chunk(p, c, a, s);
-                apply_repair(p, c, a, r, cpb);
-            }
-        } else if (nd > 0) {
-            // sort the (small) list of chunks whose last state changed, then walk forward
-            for (uint32_t i = 1; i < nd; ++i) {
-                const uint32_t vc = p.div_list[i];
-                uint32_t j = i;
-                while (j > 0 && p.div_list[j - 1] > vc) { p.div_list[j] = p.div_list[j - 1]; --j; }
-                p.div_list[j] = vc;
-            }
-            uint64_t walked = 0;
-            for (uint32_t i = 0; i < nd; ++i) {
-                const uint64_t c = p.div_list[i];
-                if (c < walked) continue;   // already recomputed from its true start
-                // the walk stops exactly where the next chunk's assumed start is the true
-                // last state of the chunk before it
-                uint32_t cur = p.last_state[c];
-                uint64_t k = c + 1;
-                for (;;) {
-                    if (k >= p.nseg || cur == p.spec_start[k]) { walked = k; break; }
-                    const Repair r = repair_chunk(p, k, cur, p.spec_start[k]);
-                    apply_repair(p, k, cur, r, cpb);
-                    p.flags[k] = 1;   // its records follow a start that was not the true one
-                    cur = r.last;
-                    ++k;
-                }
-            }
-        }
-        carry = 0;
-    }
-    __syncthreads();
-    // exclusive scan of the block sums -> output offsets; total -> out_count
-    const uint32_t nb = gridDim.x;
-    for (uint32_t base = 0; base < nb; base += THREADS) {
-        const uint32_t i = base + tid;
-        const unsigned long long v = i < nb ? p.cta_sum[i] : 0ull;
-        unsigned long long x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if ((tid & 31) >= (uint32_t)o) x += y;
-        }
-        if ((tid & 31) == 31) wsum[tid >> 5] = x;
-        __syncthreads();
-        if (tid < 32) {
-            unsigned long long t = tid < THREADS / 32 ? wsum[tid] : 0ull;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
-                if (tid >= (uint32_t)o) t += y;
-            }
-            if (tid < THREADS / 32) wsum[tid] = t;
-        }
-        __syncthreads();
-        const unsigned long long incl = x + ((tid >> 5) ? wsum[(tid >> 5) - 1] : 0ull) + carry;
-        if (i < nb) p.cta_off[i] = incl - v;
-        __syncthreads();
-        if (tid == THREADS - 1) carry = incl;
-        __syncthreads();
-    }
-    if (tid == 0) *p.out_count = carry;
-}
-
-template <int MODE, int WARPS, bool POS>
-__global__ void __launch_bounds__(WARPS * 32, 1)
-scan_kernel(ScanParams p) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint32_t warp_last[WARPS];
-    __shared__ uint4 head_s[WARPS * 32];   // each chunk's first 16 bytes, for the repair
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
-
-    // shared memory: [staging: WARPS x 4 KB][one-symbol table][compact pair table][pad][pair table]
-    uint8_t *stage_ptr = smem + (size_t)warp * kStages * kStageBytes;
-    const uint32_t stage_addr = smem_base + (uint32_t)warp * kStages * kStageBytes;
-    uint32_t *one_s = reinterpret_cast<uint32_t *>(smem + (size_t)WARPS * kStages * kStageBytes);
-
-    const uint64_t seg0 = ((uint64_t)blockIdx.x * WARPS + warp) * 32u;
-    const uint64_t seg = seg0 + lane;
-    const bool warp_busy = seg0 < p.nseg;
-    const bool active = seg < p.nseg;
-    const uint64_t S = p.seg_bytes;
-    const uint64_t b = seg * S;   // aligned offset of this chunk
-    const uint32_t ntiles = warp_busy ? (uint32_t)(S / kTile) : 0u;
-
-    // ---- staging: each warp copies tile t of its 32 chunks into a swizzled [32 rows][128 B]
-    // stage. Copy j (0..7) of a lane moves the 16-byte column lane & 7 of row 4j + lane/8,
-    // so each copy instruction of the warp covers four whole 128-byte lines. Only the warp
-    // holding the last chunk can run past the end of the sequence and checks bounds.
-    const uint32_t l8 = (uint32_t)lane >> 3, cc = (uint32_t)lane & 7u;
-    const uint64_t copy_off0 = (seg0 + l8) * S + cc * 16u;
-    const uint32_t copy_dst0 = stage_addr + l8 * kTile + ((cc ^ l8) << 4);
-    // odd copies land in rows with (row & 7) >= 4: their swizzled column differs in bit 2
-    const uint32_t copy_dst1 = stage_addr + l8 * kTile + ((cc ^ l8 ^ 4u) << 4);
-    const bool tail_warp = seg0 + 32 >= p.nseg;
-    const uint8_t *copy_src = p.abase + copy_off0;   // copy 0 of the next tile to issue
-    const uint64_t stride4 = 4u * S;                 // four chunk rows apart
-    auto issue = [&](uint32_t t) {
-        if (!tail_warp) {
-            // every row of this warp lies inside the sequence: no checks
-            const uint8_t *src = copy_src + (uint64_t)t * kTile;
-            cp_async16_full<0 * 4 * kTile>(copy_dst0, src);
-            cp_async16_full<1 * 4 * kTile>(copy_dst1, src + stride4);
-            cp_async16_full<2 * 4 * kTile>(copy_dst0, src + 2 * stride4);
-            cp_async16_full<3 * 4 * kTile>(copy_dst1, src + 3 * stride4);
-            cp_async16_full<4 * 4 * kTile>(copy_dst0, src + 4 * stride4);
-            cp_async16_full<5 * 4 * kTile>(copy_dst1, src + 5 * stride4);
-            cp_async16_full<6 * 4 * kTile>(copy_dst0, src + 6 * stride4);
-            cp_async16_full<7 * 4 * kTile>(copy_dst1, src + 7 * stride4);
-            return;
-        }
-        const uint64_t base = copy_off0 + (uint64_t)t * kTile;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint64_t goff = base + (uint64_t)j * stride4;
-            const bool ok = seg0 + 4u * j + l8 < p.nseg && goff < p.hi;
-            const uint32_t dst = ((j & 1) ? copy_dst1 : copy_dst0) + (uint32_t)j * 4u * kTile;
-            cp_async16(dst, ok ? p.abase + goff : p.abase, ok ? 16u : 0u);
-        }
-    };
-    auto prefetch = [&](uint32_t t) {   // this lane's own row of tile t into L2
-        uint64_t off = b + (uint64_t)t * kTile;
-        if (active && t < ntiles && off < p.hi) prefetch_l2(p.abase + off);
-    };
-    // the (small) compact tables are loaded first, so that these loads are not queued
-    // behind the first tile's copies
-    const uint32_t n1 = p.n_states * 4u;
-    const uint32_t nc = MODE == MODE_PAIR ? p.n_states * 16u : 0u;
-    constexpr int kPre = 2048 / (WARPS * 32) > 0 ? 2048 / (WARPS * 32) : 1;
-    uint32_t pre[kPre];
-    if constexpr (MODE != MODE_ONE_GLOBAL) {
-#pragma unroll
-        for (int r = 0; r < kPre; ++r) {
-            const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
-            pre[r] = i < n1 ? p.one[i] : (i < n1 + nc ? p.pair[i - n1] : 0u);
-        }
-    }
-    if (ntiles) issue(0);
-    cp_async_commit();
-    for (uint32_t t = 1; t < 1 + p.prefetch_tiles; ++t) prefetch(t);
-    const bool has_lookback = active && b > p.lo && p.lookback > 0;
-
-    OneTable T;
-    T.reset_entry = p.reset_entry;
-    uint32_t pair_base = 0;
-    if constexpr (MODE == MODE_ONE_GLOBAL) {
-        T.t = p.one;
-    } else {
-        // one-symbol table, then (pair mode) the compact pair table right after it
-        uint32_t *tabs = one_s;
-#pragma unroll
-        for (int r = 0; r < kPre; ++r) {
-            const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
-            if (i < n1 + nc) tabs[i] = pre[r];
-        }
-        for (uint32_t i = threadIdx.x + (uint32_t)kPre * WARPS * 32; i < n1 + nc; i += WARPS * 32)
-            tabs[i] = i < n1 ? p.one[i] : p.pair[i - n1];
-        T.t = one_s;
-        if (MODE == MODE_PAIR) {
-            // every lane's copy of the pair table is expanded from the compact copy
-            const uint32_t *cbuf = one_s + n1;
-            uint32_t after_c = smem_base + (uint32_t)WARPS * kStages * kStageBytes + (n1 + nc) * 4u;
-            pair_base = (after_c + 2047u) & ~2047u;   // bits 0..10 of the base are zero
-            uint32_t *pair_ptr = reinterpret_cast<uint32_t *>(smem + (pair_base - smem_base));
-            __syncthreads();
-            const uint32_t n2 = p.n_states * 16u * 32u;
-            for (uint32_t i = threadIdx.x; i < n2; i += WARPS * 32) {
-                uint32_t e = cbuf[i >> 5];
-                uint32_t nx = e & 0x00FFFFFFu, c = e >> 24;
-                pair_ptr[i] = (c << kCountShift) | (pair_base + nx * (uint32_t)kPairRowBytes + (i & 31u) * 4u);
-            }
-        }
-    }
-    __syncthreads();
-    uint32_t *stash = POS ? p.stash + seg * (kStashCap * 3) : nullptr;
-    uint32_t nrec = 0;
-
-    // ---- speculated start state: q0, or the state reached from q0 over the lookback window
-    uint32_t q = 0;
-    if (has_lookback) {   // the 'lookback' bytes in front of the chunk
-        const uint64_t from = b - p.lo > p.lookback ? b - p.lookback : p.lo;
-        for (uint64_t off = from; off < b; ++off) q = T.step(q, p.abase[off]) & 0x7FFFFFFFu;
-    }
-    uint32_t spec = q;
-    uint32_t cnt = 0;
-    uint32_t cur = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
-
-    // tiles [t_full0, t_full1) of this chunk lie entirely inside the sequence; tiles from
-    // t_live on lie past its end (only the last chunk has any)
-    uint32_t t_live = 0, t_full0 = 0, t_full1 = 0;
-    if (active) {
-        const uint64_t rem = p.hi - b;
-        t_live = rem >= S ? ntiles : (uint32_t)((rem + kTile - 1) / kTile);
-        t_full1 = rem >= S ? ntiles : (uint32_t)(rem / kTile);
-        t_full0 = b < p.lo ? 1u : 0u;
-    }
-    const uint32_t lut_lo = p.lut_lo, lut_hi = p.lut_hi;
-    for (uint32_t t = 0; t < ntiles; ++t) {
-        cp_async_wait<0>();
-        __syncwarp();   // tile t of all 32 rows is visible to the warp
-        const uint64_t row_off = b + (uint64_t)t * kTile;
-        const bool live = t < t_live;
-        const bool full = t >= t_full0 && t < t_full1;
-        uint32_t w[32];
-        {
-            // the lane's row, un-swizzled: 16-byte chunk c sits at slot c ^ (lane & 7)
-            const uint8_t *srow = stage_ptr + lane * kTile;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                uint4 v = *reinterpret_cast<const uint4 *>(srow + ((c ^ (lane & 7)) * 16));
-                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
-            }
-        }
-        __syncwarp();   // every lane holds its row: the stage can be refilled
-        if (t + 1 < ntiles) issue(t + 1);
-        cp_async_commit();
-        if (p.prefetch_tiles) prefetch(t + 1 + p.prefetch_tiles);
-        if (t == 0) head_s[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
-        if (!live) continue;
-
-        if (MODE == MODE_PAIR) {
-            bool done = false;
-            if (full) {
-                uint32_t acc = 0, err = 0, rc = 0, c2 = cur;
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    // codes of the 4 bytes sit at bits 1..2 of each byte of x; y = x*65
-                    // puts the first pair at bits 7..10 and the second at bits 23..26, and
-                    // is zero at bits 27..30, so the mux below forms clean addresses
-                    const uint32_t x = w[k] & 0x06060606u;
-                    const uint32_t y = mad_lo(x, 65u, 0u);
-                    const uint32_t e1 = lds_u32(mux_pair(c2, y));
-                    const uint32_t e2 = lds_u32(mux_pair(e1, y >> 16));
-                    acc = mad_lo(e1, p.k1, acc);
-                    acc = mad_lo(e2, p.k1, acc);
-                    c2 = e2;
-                    if (k % 3 == 2 || k == 31) {     // <= 6 entries: count <= 12 fits bits 27..30
-                        rc = mad_hi(acc, p.k5, rc);  // rc += acc >> 27
-                        acc = 0;
-                    }
-                    // bit-exact base check: expected lowercase bytes selected by the codes
-                    const uint32_t z = x | (x >> 4);
-                    const uint32_t sel = __byte_perm(z, 0, 0x0020);
-                    const uint32_t expect = __byte_perm(lut_lo, lut_hi, sel);
-                    err |= expect ^ w[k];
-                }
-                if ((err & 0xDFDFDFDFu) == 0) {
-                    if (POS && rc)
-                        record_hit_row(stash, nrec, t,
-                                       ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes, cnt);
-                    cnt += rc;
-                    cur = c2 & 0x3FFFFu;
-                    done = true;
-                }
-            }
-            if (!done) {
-                uint32_t qs = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-                uint32_t before = cnt;
-                // a reset byte or a sequence edge in this row: walk it from global memory
-                // (the row was just staged, so it is in L2)
-                uint32_t qe = row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
-                                               row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
-                if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
-                cur = pair_base + qe * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
-            }
-        } else {
-            uint32_t before = cnt, qs = q;
-            q = full ? row_bytes_reg(T, qs, w, cnt)
-                     : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
-                                        row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
-            if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
-        }
-    }
-    cp_async_wait<0>();
-    uint32_t last = q;
-    if (MODE == MODE_PAIR) last = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-
-    // ---- join inside the block (Sec. III-A) with repair at the converging point (Alg. 1):
-    // the true start of a chunk is the last state of the chunk before it, which the lane
-    // to the left (or, for lane 0, the previous warp's lane 31) has just computed
-    if (lane == 31) warp_last[warp] = last;
-    __syncthreads();
-    uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, last, 1);
-    if (lane == 0) prev = warp > 0 ? warp_last[warp - 1] : 0u;
-    const bool has_prev = active && seg > 0 && (lane > 0 || warp > 0);
-    bool pending = active && seg > 0 && !has_prev;   // first chunk of the block
-    if (has_prev && prev != spec) {
-        // run the true start and the speculated start in lockstep over the chunk's first
-        // bytes; at the first step where their states are equal, the rest of the chunk is
-        // identical for both runs
-        const uint64_t vlen64 = p.hi - b;
-        const uint32_t vlen = vlen64 < 16 ? (uint32_t)vlen64 : 16u;
-        const uint4 h4 = head_s[threadIdx.x];   // the chunk's first 16 bytes
-        const uint32_t head[4] = {h4.x, h4.y, h4.z, h4.w};
-        uint32_t qa = prev, qs = spec, pa = 0, ps = 0;
-        bool conv = false;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (!conv && (uint32_t)k < vlen) {
-                const uint32_t byte = (head[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-                const uint32_t ea = T.step(qa, byte), es = T.step(qs, byte);
-                qa = ea & 0x7FFFFFFFu; qs = es & 0x7FFFFFFFu;
-                pa += ea >> 31; ps += es >> 31;
-                conv = qa == qs;
-            }
-        }
-        if (conv) {
-            const uint32_t delta = pa - ps;   // modulo 2^32; the corrected count is exact
-            cnt += delta;
-            if (POS) fix_hit_rows(stash, nrec, prev, delta, pa);
-            spec = prev;
-        } else {
-            pending = true;   // the last block repairs it from global memory
-        }
-    }
-    if (active) {
-        p.spec_start[seg] = spec;
-        p.last_state[seg] = last;
-        p.count[seg] = cnt;
-        p.flags[seg] = 0;
-        if (POS) p.nrec[seg] = nrec;
-    }
-    if (pending) {
-        const uint32_t k = atomicAdd(&p.ctrl[1], 1u);
-        if (k < p.pending_cap) p.pending[k] = (uint32_t)seg;
-    }
-    __threadfence();   // this thread's results are visible before the block's ticket
-    // block sum of the chunk counts
-    unsigned long long v = active ? cnt : 0u;
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    __shared__ unsigned long long red[WARPS];
-    __shared__ int is_last;
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int i = 0; i < WARPS; ++i) t += red[i];
-        p.cta_sum[blockIdx.x] = t;
-        __threadfence();
-        is_last = atomicAdd(&p.ctrl[0], 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    finalize_block<WARPS * 32>(p);
-}
 
 // ------------------------------------------------------------ extraction
 
@@ -914,15 +358,10 @@ size_t scan_total_smem(int mode, int warps, uint32_t n_states) {
     return scan_smem_bytes(mode, warps, n_states) + scan_static_smem(warps);
 }
 
-using ScanFn = void (*)(ScanParams);
-
 ScanFn scan_fn(int mode, int warps, bool pos) {
-#define PICK(M, W)                                                   \
-    if (mode == M && warps == W) return pos ? scan_kernel<M, W, true> : scan_kernel<M, W, false>;
-    PICK(MODE_PAIR, 8) PICK(MODE_PAIR, 16) PICK(MODE_PAIR, 24) PICK(MODE_PAIR, 32)
-    PICK(MODE_ONE_SMEM, 8) PICK(MODE_ONE_SMEM, 16) PICK(MODE_ONE_SMEM, 24) PICK(MODE_ONE_SMEM, 32)
-    PICK(MODE_ONE_GLOBAL, 8) PICK(MODE_ONE_GLOBAL, 16) PICK(MODE_ONE_GLOBAL, 24) PICK(MODE_ONE_GLOBAL, 32)
-#undef PICK
+    if (mode == MODE_PAIR) return scan_fn_pair(warps, pos);
+    if (mode == MODE_ONE_SMEM) return scan_fn_one_smem(warps, pos);
+    if (mode == MODE_ONE_GLOBAL) return scan_fn_one_global(warps, pos);
     return nullptr;
 }
 
