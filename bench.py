@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batch-runs", type=int, default=10)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-percall", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -299,6 +301,101 @@ def bench_batched(args, dna, torch, stream, clocks_mhz):
 
 
 
+SERVE_WORKLOAD = ("serving: Poisson arrivals at 2,000 req/s (seed 4), lengths log-uniform 4 KiB..64 MiB, "
+                  "slices of a 256 MiB order-2 Markov sequence with soft-masked and N runs in pinned host "
+                  "memory; 16 resident automata (8 Aho-Corasick sets of 8-16-mers <= 500 states, 8 motif "
+                  "regexes); 8 slots, 40 GiB admission cap")
+
+
+def serve_automata(dna):
+    """16 automata: 8 k-mer sets (random 8..16-mers, as many as keep <= 500 states) and
+    8 motif regexes."""
+    import synth
+    dfas, kinds = [], []
+    for i in range(8):
+        n = 40
+        while True:
+            km = synth.random_kmers(400 + i, n, 8, 16)
+            q = dna.compile_kmers(km)[0].shape[0]
+            if q <= 500 or n <= 4:
+                break
+            n -= 4
+        dfas.append(dna.Dfa.from_kmers(km))
+        kinds.append(("kmers", n, q))
+    for r in synth.random_regexes(4, 8):
+        d = dna.Dfa.from_regex(r)
+        dfas.append(d)
+        kinds.append(("regex", r, d.info().n_states))
+    return dfas, kinds
+
+
+def bench_serve(args, dna, torch):
+    import synth
+    n_pay = 256 * MiB
+    payload = synth.markov2(4, n_pay)
+    synth.overlay_runs(payload, 4, 0.10, 1000.0, "lower")
+    synth.overlay_runs(payload, 5, 0.02, 50000.0, "N")
+    pinned = torch.from_numpy(payload).pin_memory()
+    dfas, kinds = serve_automata(dna)
+    n_req = args.serve_requests
+    rng = np.random.Generator(np.random.PCG64(4))
+    lens = synth.log_uniform_lengths(4, n_req, 4 * 1024, 64 * MiB)
+    offs = np.array([int(rng.integers(0, n_pay - n + 1)) for n in lens], np.int64)
+    didx = rng.integers(0, len(dfas), n_req)
+    gaps = rng.exponential(1e9 / 2000.0, n_req)
+    srv = dna.Server(dfas, slots=8, mem_cap_bytes=40 << 30)
+    base = pinned.data_ptr()
+    # warm the slots (first-call set-up of each kernel variant), then the timed schedule
+    for i in range(16):
+        srv.submit((base, 1 << 20), i % len(dfas))
+    srv.drain()
+    srv.poll(64)
+    t0 = dna.Server.now_ns() + 50_000_000
+    arrivals = (t0 + np.cumsum(gaps)).astype(np.int64)
+    ids = {}
+    for i in range(n_req):
+        ids[srv.submit((base + int(offs[i]), int(lens[i])), int(didx[i]), int(arrivals[i]))] = i
+    srv.drain()
+    comps = srv.poll(max_items=n_req + 16)
+    srv.free()
+    assert len(comps) == n_req
+    res = [None] * n_req
+    for c in comps:
+        res[ids[c["id"]]] = c
+    lat = np.array([(c["done_ns"] - c["arrival_ns"]) / 1e6 for c in res])
+    lat_noh2d = np.array([(c["done_ns"] - c["arrival_ns"]) / 1e6 - c["h2d_us"] / 1e3 for c in res])
+    dev = np.array([c["device_us"] / 1e3 for c in res])
+    span_s = (max(c["done_ns"] for c in res) - min(c["arrival_ns"] for c in res)) / 1e9
+    total = int(lens.sum())
+    # every count against one dna_scan of the same slice on the device
+    dpay = pinned.cuda()
+    out = torch.empty(n_req, dtype=torch.int64, device="cuda")
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    for i in range(n_req):
+        dna.scan_ptr(dfas[int(didx[i])], dpay.data_ptr() + int(offs[i]), int(lens[i]), out.data_ptr() + 8 * i, sh)
+    torch.cuda.synchronize()
+    same = bool(np.array_equal(out.cpu().numpy(), np.array([c["count"] for c in res], np.int64)))
+    ok = all(c["status"] == 0 for c in res)
+    ev = sorted([(c["admit_ns"], 1) for c in res] + [(c["done_ns"], -1) for c in res])
+    conc = peak = 0
+    for _, d in ev:
+        conc += d
+        peak = max(peak, conc)
+    del dpay
+    return {
+        "workload": SERVE_WORKLOAD, "requests": n_req, "bytes": total,
+        "offered_gbs": total / (float(gaps.sum()) / 1e9) / 1e9,
+        "gbs": total / span_s / 1e9, "span_s": span_s,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "p50_ms_without_h2d": float(np.percentile(lat_noh2d, 50)),
+        "p99_ms_without_h2d": float(np.percentile(lat_noh2d, 99)),
+        "device_p50_ms": float(np.percentile(dev, 50)), "device_p99_ms": float(np.percentile(dev, 99)),
+        "max_concurrent": peak, "all_ok": ok, "identical_to_single_calls": same,
+        "automata_states": [k[2] for k in kinds],
+    }
+
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -417,6 +514,10 @@ def main():
     if world == 1 and not args.no_batched:
         batched = bench_batched(args, dna, torch, stream, clocks.get("sm_mhz"))
 
+    serve = None
+    if world == 1 and not args.no_serve:
+        serve = bench_serve(args, dna, torch)
+
     info = dfa.info()
     if rank == 0:
         line = {
@@ -437,6 +538,7 @@ def main():
                     "api": "dna_scan_host (pinned host buffers, synchronous)"},
             "gpu_launches": launches,
             "batched": batched,
+            "serve": serve,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -270,6 +270,79 @@ int dna_scan_batch(const dna_dfa *const *dfas, uint32_t n_dfas,
                    const uint8_t *const *seqs, const uint64_t *lens, uint32_t n_seqs,
                    dna_stream_t stream, uint64_t *out_counts);
 
+/*
+ * Request loop (serving): scans of mixed sizes against resident automata, admitted
+ * continuously. A server owns 'slots' CUDA streams, a device memory pool and a
+ * dispatcher thread. Submitted requests wait in arrival order; the dispatcher admits
+ * the head request once its arrival time has passed, a slot is free and the memory it
+ * needs (its length rounded up to 4 KiB, plus 1 MiB of scan scratch) fits under
+ * mem_cap_bytes. An admitted request copies its sequence to the device, runs the count
+ * scan of dna_scan and copies the count back, all on its slot's stream, so requests
+ * in different slots overlap on the device. The paper scans one input at a time; this
+ * is the serving form of that scan (no paper counterpart).
+ *
+ * dna_server_create -- dfas: host array of n_dfas handles (loaded on the current
+ *   device; they stay resident and must outlive the server). opts may be NULL:
+ *   slots (default 8, at most 256) and mem_cap_bytes (default 40 GiB).
+ */
+typedef struct {
+    uint32_t slots;
+    uint64_t mem_cap_bytes;
+} dna_server_opts;
+
+typedef struct dna_server dna_server; /* opaque */
+
+int dna_server_create(const dna_dfa *const *dfas, uint32_t n_dfas, const dna_server_opts *opts,
+                      dna_server **out);
+
+/*
+ * dna_server_submit -- queues a scan of host_seq[0, len) with automaton 'dfa' (an index
+ *   into the server's array). host_seq should be pinned host memory (a pageable buffer
+ *   makes the copy synchronous and stalls the dispatcher); it must stay valid and
+ *   unchanged until the request's completion is reported. arrival_ns = 0 means now;
+ *   otherwise a dna_server_now_ns() time before which the request is not admitted
+ *   (open-loop load generation). Returns the request id (>= 0) or a negative DNA_ERR_*.
+ */
+int64_t dna_server_submit(dna_server *server, const uint8_t *host_seq, uint64_t len, uint32_t dfa,
+                          uint64_t arrival_ns);
+
+/* A finished request. Times are dna_server_now_ns() values. */
+typedef struct {
+    int64_t  id;
+    int32_t  status;      /* DNA_OK, or the request's error (DNA_ERR_CAPACITY when it can never fit the cap) */
+    uint32_t dfa;
+    uint64_t count;       /* the dna_scan count */
+    uint64_t len;
+    uint64_t arrival_ns;  /* scheduled (or submit) time */
+    uint64_t admit_ns;    /* when the dispatcher queued its work */
+    uint64_t done_ns;     /* when the dispatcher saw its work complete */
+    float    h2d_us;      /* device time of the host-to-device copy */
+    float    device_us;   /* device time of copy + scan + result copy */
+} dna_completion;
+
+/* dna_server_poll -- moves up to max finished requests to out, waiting up to timeout_ms
+ * (0 = no wait, < 0 = until one finishes) when none is ready. Returns how many. */
+int dna_server_poll(dna_server *server, dna_completion *out, uint32_t max, int32_t timeout_ms);
+
+/* dna_server_drain -- waits until every submitted request has finished (timeout_ms < 0:
+ * no limit). DNA_ERR_TIMEOUT when the limit passes first. */
+int dna_server_drain(dna_server *server, int32_t timeout_ms);
+
+typedef struct {
+    uint64_t submitted, completed, queued;
+    uint32_t in_flight, slots;
+    uint64_t mem_in_use, mem_cap;
+} dna_server_stats_t;
+
+int dna_server_stats(dna_server *server, dna_server_stats_t *out);
+
+/* dna_server_now_ns -- the server clock (steady, nanoseconds). */
+uint64_t dna_server_now_ns(void);
+
+/* dna_server_free -- finishes every queued request, stops the dispatcher and releases
+ * the server. NULL is ignored. */
+void dna_server_free(dna_server *server);
+
 /* dna_status_string -- a static description of a status code. */
 const char *dna_status_string(int status);
 

@@ -25,6 +25,8 @@ EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
     "dna_scan_count_static", "dna_scan_host",
     "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
+    "dna_server_create", "dna_server_submit", "dna_server_poll", "dna_server_drain",
+    "dna_server_stats", "dna_server_now_ns", "dna_server_free",
     "dna_status_string", "dna_compile_regex", "dna_compile_kmers", "dna_free_host",
     "dna_profile_enable", "dna_profile_read",
 ]
@@ -68,6 +70,23 @@ class _BatchInfo(ctypes.Structure):
                 ("n_fast", ctypes.c_uint32), ("n_slow", ctypes.c_uint32),
                 ("n_chunks", ctypes.c_uint64), ("packed_tiles", ctypes.c_uint64),
                 ("max_states", ctypes.c_uint32)]
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("mem_cap_bytes", ctypes.c_uint64)]
+
+
+class _Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("dfa", ctypes.c_uint32),
+                ("count", ctypes.c_uint64), ("len", ctypes.c_uint64), ("arrival_ns", ctypes.c_uint64),
+                ("admit_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64),
+                ("h2d_us", ctypes.c_float), ("device_us", ctypes.c_float)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("in_flight", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("mem_in_use", ctypes.c_uint64), ("mem_cap", ctypes.c_uint64)]
 
 
 def build(force: bool = False) -> str:
@@ -114,6 +133,20 @@ def lib():
         L.dna_batch_info.restype = i32
         L.dna_batch_free.argtypes = [p]
         L.dna_batch_free.restype = None
+        L.dna_server_create.argtypes = [p, u32, ctypes.POINTER(_ServerOpts), ctypes.POINTER(p)]
+        L.dna_server_create.restype = i32
+        L.dna_server_submit.argtypes = [p, p, u64, u32, u64]
+        L.dna_server_submit.restype = ctypes.c_int64
+        L.dna_server_poll.argtypes = [p, ctypes.POINTER(_Completion), u32, ctypes.c_int32]
+        L.dna_server_poll.restype = i32
+        L.dna_server_drain.argtypes = [p, ctypes.c_int32]
+        L.dna_server_drain.restype = i32
+        L.dna_server_stats.argtypes = [p, ctypes.POINTER(_ServerStats)]
+        L.dna_server_stats.restype = i32
+        L.dna_server_now_ns.argtypes = []
+        L.dna_server_now_ns.restype = u64
+        L.dna_server_free.argtypes = [p]
+        L.dna_server_free.restype = None
         L.dna_scan_batch.argtypes = [p, u32, p, p, u32, p, p]
         L.dna_scan_batch.restype = i32
         L.dna_status_string.argtypes = [i32]
@@ -430,6 +463,76 @@ class Batch:
         if self._h:
             lib().dna_batch_free(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """The request loop (dna_server_*): scans of host sequences against resident automata,
+    admitted continuously into 'slots' device streams under a device-memory cap."""
+
+    def __init__(self, dfas, slots: int = 8, mem_cap_bytes: int = 40 << 30):
+        self._dfas = list(dfas)
+        hs = (ctypes.c_void_p * len(self._dfas))(*[d.handle for d in self._dfas])
+        opts = _ServerOpts(slots, mem_cap_bytes)
+        h = ctypes.c_void_p()
+        _check(lib().dna_server_create(ctypes.cast(hs, ctypes.c_void_p), len(self._dfas), ctypes.byref(opts),
+                                       ctypes.byref(h)), "dna_server_create")
+        self._h = h
+        self._keep = {}
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(lib().dna_server_now_ns())
+
+    def submit(self, seq, dfa: int, arrival_ns: int = 0, keep=None) -> int:
+        """Queues a scan of a host uint8 buffer (numpy array or pinned CPU tensor, or a raw
+        (pointer, length) pair). 'keep' holds a reference until the request finishes."""
+        import torch
+        if isinstance(seq, tuple):
+            ptr, n = seq
+        elif isinstance(seq, np.ndarray):
+            ptr, n = seq.ctypes.data, seq.size
+        elif isinstance(seq, torch.Tensor) and not seq.is_cuda:
+            ptr, n = seq.data_ptr(), seq.numel()
+        else:
+            raise TypeError("seq must be host memory")
+        rid = int(lib().dna_server_submit(self._h, ptr, n, dfa, arrival_ns))
+        if rid < 0:
+            raise DnaError(rid, "dna_server_submit")
+        if keep is not None:
+            self._keep[rid] = keep
+        return rid
+
+    def poll(self, max_items: int = 1024, timeout_ms: int = 0) -> list[dict]:
+        buf = (_Completion * max_items)()
+        n = lib().dna_server_poll(self._h, buf, max_items, timeout_ms)
+        if n < 0:
+            raise DnaError(n, "dna_server_poll")
+        out = []
+        for i in range(n):
+            c = buf[i]
+            self._keep.pop(c.id, None)
+            out.append({k: getattr(c, k) for k, _ in _Completion._fields_})
+        return out
+
+    def drain(self, timeout_ms: int = -1):
+        _check(lib().dna_server_drain(self._h, timeout_ms), "dna_server_drain")
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().dna_server_stats(self._h, ctypes.byref(st)), "dna_server_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def free(self):
+        if self._h:
+            lib().dna_server_free(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -1,0 +1,115 @@
+"""GPU tests of the request loop (dna_server_*): every request's count equals the
+oracle's, both when the requests run alone (one slot, one at a time) and when they run
+mixed (many slots, memory-capped admission, requests overlapping on the device); the
+admission cap and the open-loop arrival schedule are honoured."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1509_01506_gb300 as dna
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KiB, MiB = 1 << 10, 1 << 20
+
+
+def request_bytes(n):
+    # the server's charge per request: the sequence rounded up to 4 KiB plus 1 MiB
+    return ((n + 4095) // 4096) * 4096 + MiB
+
+
+@pytest.fixture(scope="module")
+def workload():
+    pats = [("regex", p) for p in synth.random_regexes(21, 4)]
+    pats += [("kmers", synth.random_kmers(22 + i, 12, 8, 16)) for i in range(4)]
+    payload = synth.markov2(23, 48 * MiB)
+    synth.overlay_runs(payload, 23, 0.05, 500.0, "lower")
+    synth.overlay_runs(payload, 24, 0.01, 5000.0, "N")
+    pinned = torch.from_numpy(payload).pin_memory()
+    rng = np.random.default_rng(25)
+    n_req = 120
+    lens = synth.log_uniform_lengths(26, n_req, 4 * KiB, 4 * MiB)
+    offs = [int(rng.integers(0, payload.size - n)) for n in lens]
+    dfa_idx = rng.integers(0, len(pats), n_req).tolist()
+    tables = [oracle.compile_regex(p) if k == "regex" else oracle.compile_kmers(p, minimise=True)
+              for k, p in pats]
+    want = [oracle.run(*tables[d], payload[o:o + int(n)], positions=False)[0]
+            for o, n, d in zip(offs, lens, dfa_idx)]
+    dfas = [dna.Dfa.from_regex(p) if k == "regex" else dna.Dfa.from_kmers(p) for k, p in pats]
+    return pinned, lens, offs, dfa_idx, want, dfas
+
+
+def run_server(workload, slots, cap, arrivals=None):
+    pinned, lens, offs, dfa_idx, _, dfas = workload
+    srv = dna.Server(dfas, slots=slots, mem_cap_bytes=cap)
+    base = pinned.data_ptr()
+    out = {}
+    for i, (o, n, d) in enumerate(zip(offs, lens, dfa_idx)):
+        rid = srv.submit((base + o, int(n)), d, 0 if arrivals is None else arrivals[i])
+        out[rid] = i
+        if slots == 1 and arrivals is None:
+            srv.drain()     # alone: the next request is submitted after this one finished
+    srv.drain()
+    comps = srv.poll(max_items=len(lens) + 8)
+    assert len(comps) == len(lens)
+    srv.free()
+    res = [None] * len(lens)
+    for c in comps:
+        res[out[c["id"]]] = c
+    return res
+
+
+def test_results_alone_and_in_the_mix_equal_the_oracle(workload):
+    _, lens, _, _, want, _ = workload
+    alone = run_server(workload, slots=1, cap=1 << 30)
+    cap = 24 * MiB
+    mix = run_server(workload, slots=8, cap=cap)
+    assert [c["status"] for c in alone] == [0] * len(lens)
+    assert [c["status"] for c in mix] == [0] * len(lens)
+    assert [c["count"] for c in alone] == want
+    assert [c["count"] for c in mix] == want
+    # the mix overlapped requests on the device, and never admitted more than the cap
+    ev = sorted([(c["admit_ns"], request_bytes(c["len"])) for c in mix] +
+                [(c["done_ns"], -request_bytes(c["len"])) for c in mix], key=lambda x: (x[0], x[1]))
+    in_use = peak = conc = max_conc = 0
+    for _, b in ev:
+        in_use += b
+        conc += 1 if b > 0 else -1
+        peak = max(peak, in_use)
+        max_conc = max(max_conc, conc)
+    assert peak <= cap
+    assert max_conc >= 2
+
+
+def test_open_loop_arrivals_are_honoured(workload):
+    _, lens, _, _, want, _ = workload
+    rng = np.random.default_rng(27)
+    t0 = dna.Server.now_ns() + 20_000_000
+    arrivals = (t0 + np.cumsum(rng.exponential(1e9 / 2000.0, len(lens)))).astype(np.int64).tolist()
+    res = run_server(workload, slots=4, cap=1 << 30, arrivals=arrivals)
+    assert [c["count"] for c in res] == want
+    assert all(c["admit_ns"] >= c["arrival_ns"] for c in res)
+    assert all(c["done_ns"] >= c["admit_ns"] for c in res)
+
+
+def test_request_larger_than_the_cap_fails_alone(workload):
+    pinned, _, _, _, _, dfas = workload
+    srv = dna.Server(dfas[:1], slots=2, mem_cap_bytes=4 * MiB)
+    big = srv.submit((pinned.data_ptr(), 8 * MiB), 0)
+    small = srv.submit((pinned.data_ptr(), 64 * KiB), 0)
+    srv.drain(timeout_ms=20000)
+    comps = {c["id"]: c for c in srv.poll(16)}
+    assert comps[big]["status"] == -3
+    assert comps[small]["status"] == 0
+    payload = pinned[:64 * KiB].numpy()
+    t, a = oracle.compile_regex(synth.random_regexes(21, 1)[0])
+    assert comps[small]["count"] == oracle.run(t, a, payload, positions=False)[0]
+    srv.free()
+    with pytest.raises(dna.DnaError):
+        s2 = dna.Server(dfas[:1])
+        try:
+            s2.submit((pinned.data_ptr(), 100), 5)
+        finally:
+            s2.free()
