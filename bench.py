@@ -408,6 +408,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     import paper_1509_01506_gb300 as dna
+    from paper_1509_01506_gb300 import shard
     import synth
 
     seq_np, pattern = synth.plain_markov(args.bytes)
@@ -449,10 +450,7 @@ def main():
     launches = dna.profile_read(reset=True)["kernel_launches"]
     clocks = sampler.stop()
     ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = shard.max_over_ranks(ms_total, device="cuda")   # the slowest rank
     ms_step = ms_total / args.steps
     value = n * world / (ms_step * 1e-3) / 1e9
 
@@ -486,10 +484,7 @@ def main():
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     barrier()
     assert c_host == n_matches
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, device="cuda")
     e2e_value = n * world / (e2e_ms * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel (the chunk scan), timed live with events

@@ -48,7 +48,8 @@
 
 /* ---------------------------------------------------------------- symbols */
 
-/* Byte -> symbol, reading G8: case-insensitive bases, everything else resets. */
+/* Byte -> symbol: case-insensitive bases; every other byte is the reset symbol (the
+ * paper never mentions non-base bytes; N and IUPAC codes are read as breaking a match). */
 int or_symbol_of_byte(int byte)
 {
     switch (byte) {

@@ -1,17 +1,16 @@
-// dna_scan.cu -- GB300 (sm_103a) kernels and the C ABI of the DNA automaton scan.
+// dna_scan.cu -- host side of the single-sequence path (planning, scratch, launches),
+// the position-extraction kernel and the C ABI of the automata and scans.
 //
 // The data-parallel path of Memeti & Pllana (Sec. III-A, III-B, Alg. 1), re-designed
-// for one GPU:
+// for one GPU (the chunk-scan kernel itself is in scan_kernel.cuh):
 //   * Input-based partitioning (Sec. III-A, Fig. 1a): the sequence is cut into chunks of
 //     chunk_bytes; every GPU lane owns one chunk. A warp's 32 chunks are staged into
 //     shared memory tile by tile with cp.async (16-byte copies; each copy instruction
 //     of the warp covers four whole 128-byte lines) and read back row by row.
 //   * Speculation (Sec. III-A, possible starting states): a chunk's start state is
-//     unknown; the lane runs the automaton from q0 over the 'lookback' symbols in front
-//     of its chunk. The state it reaches lies in the set of possible starting states
-//     (the image of all states under those symbols), and is the exact start whenever
-//     the automaton is lookback-definite, a reset byte occurs in the window, or the
-//     window reaches the sequence start.
+//     unknown. By default the lane starts it in q0; with a lookback window it runs
+//     from q0 over the symbols in front of the chunk, which gives the exact start when
+//     the automaton is definite within the window.
 //   * Chunk scan (Alg. 1, the per-character loop): ingest is fused -- bytes are mapped
 //     to 2-bit codes in registers, 4 bytes at a time, with a bit-exact check that every
 //     byte is a base. Small automata use a two-symbol transition table replicated once
@@ -20,16 +19,17 @@
 //     of accepting steps in the pair. Rows with reset bytes or sequence edges take a
 //     per-byte path.
 //   * Join (the "binary reduction" of Sec. III-A) and converging point (Sec. III-B.3):
-//     a resolve kernel compares each chunk's speculated start with the previous chunk's
-//     last state. On a mismatch it runs the true start and the speculated start in
-//     lockstep from the chunk start until they meet (the converging point) and
-//     corrects the count by the paper's formula: own prefix count + speculative total
-//     - speculative prefix count at the meeting step. A run that never meets changes
-//     the chunk's last state; a cascade pass then walks forward until the chain agrees
-//     again.
+//     inside a block, each chunk's true start is its left neighbour's last state; on a
+//     mismatch the lane runs the true and the speculated start in lockstep over the
+//     chunk's first 16 bytes, and where they meet corrects the count by the paper's
+//     formula (own prefix count + speculative total - speculative prefix count). The
+//     block that finishes last joins across blocks and repairs, from global memory,
+//     the chunks whose runs did not meet early; a cascade follows a changed last state
+//     forward until the chain agrees again.
 //   * Extraction: a block scan of the chunk counts gives each chunk its output offset;
-//     positions recorded in a per-chunk stash are written in order, chunks that
-//     overflowed the stash or were corrected are rescanned from their true start.
+//     positions are re-walked from the hit rows recorded during the scan, and chunks
+//     that overflowed their records or were corrected late are rescanned from their
+//     true start.
 
 #include <cuda_runtime.h>
 

@@ -75,7 +75,8 @@ def random_seq(rng, n, p_reset=0.03, p_lower=0.2):
 
 
 def test_symbol_mapping_all_bytes():
-    """Reading G8: exactly A/a, C/c, G/g, T/t are bases; every other byte resets."""
+    """Exactly A/a, C/c, G/g, T/t are bases; every other byte resets (the reading of
+    non-base bytes the oracle takes)."""
     want = {ord("A"): 0, ord("a"): 0, ord("C"): 1, ord("c"): 1,
             ord("G"): 2, ord("g"): 2, ord("T"): 3, ord("t"): 3}
     for b in range(256):
@@ -227,7 +228,7 @@ def test_chunked_join_reproduces_sequential_run():
 
 
 def test_reset_byte_splits_the_result():
-    """Reading G8: a reset byte returns every run to q0, so the result on s1 N s2 is
+    """A reset byte returns every run to q0, so the result on s1 N s2 is
     the result on s1 followed by the result on s2 shifted by len(s1) + 1."""
     rng = np.random.default_rng(8)
     t, a = oracle.compile_regex("A(C|G)*T")
