@@ -63,6 +63,7 @@ struct EmitParams {
     const unsigned long long *cta_off;
     uint64_t *out;
     uint64_t cap;
+    uint32_t lut_lo, lut_hi;   // expected lowercase bytes per code, for the base check
 };
 
 constexpr int kEmitWalkers = 256;    // threads of an extraction block that walk rows
@@ -90,7 +91,52 @@ __device__ __forceinline__ void stage_row(uint8_t *slot, const uint8_t *abase, u
 // previous chunk's last state). The walk maps each byte through a 256-entry class table
 // (A, C, T, G -> code, anything else -> 4) and a five-column transition table whose fifth
 // column is the reset symbol.
-__global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_in_smem) {
+// Walks one whole 128-byte row of bases with the two-symbol table 'ptab' (entry: next
+// state | accept after the first symbol << 30 | accept after the second << 31), writing
+// the accepting positions from output index o. Returns false (and writes nothing) when
+// some byte of the row is not a base; the caller then walks it byte by byte.
+__device__ __forceinline__ bool walk_row_pairs(const EmitParams &p, const uint32_t *ptab, uint64_t rs,
+                                               uint32_t q, unsigned long long o) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.abase + rs);
+    uint32_t err = 0;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {   // check first: no position is written for a mixed row
+        const uint4 v = src[h];
+        const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t x = ww[i] & 0x06060606u;
+            const uint32_t z = x | (x >> 4);
+            err |= __byte_perm(p.lut_lo, p.lut_hi, __byte_perm(z, 0, 0x0020)) ^ ww[i];
+        }
+    }
+    if (err & 0xDFDFDFDFu) return false;
+    const uint64_t pos0 = rs - p.lo;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        uint4 v[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) v[h] = src[4 * half + h];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const uint32_t w = i % 4 == 0 ? v[i / 4].x : i % 4 == 1 ? v[i / 4].y : i % 4 == 2 ? v[i / 4].z : v[i / 4].w;
+            const uint32_t y = (w & 0x06060606u) * 65u;   // pair codes at bits 7..10 and 23..26
+            const uint64_t pw = pos0 + 64u * half + 4u * i;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint32_t e = ptab[q * 16u + ((y >> (j ? 23 : 7)) & 15u)];
+                q = e & 0x3FFFFFFFu;
+                if (e >> 30) {
+                    if (e & (1u << 30)) { if (o < p.cap) p.out[o] = pw + 2u * j; ++o; }
+                    if (e >> 31) { if (o < p.cap) p.out[o] = pw + 2u * j + 1u; ++o; }
+                }
+            }
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_in_smem, uint32_t ptab_in_smem) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ unsigned long long wsum[32];
     __shared__ uint32_t wsum2[32];
@@ -102,6 +148,7 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(dsm + kEmitWalkers * kEmitRowPitch);
     uint32_t *s_slot = reinterpret_cast<uint32_t *>(s_off + nthr);
     uint32_t *tab5 = s_slot + nthr + 1;
+    uint32_t *ptab = tab5 + (tab5_in_smem ? p.n_states * 5u : 0u);
     if (tid < 256) {
         const uint32_t c = (tid >> 1) & 3u;
         cls[tid] = byte_is_base(tid) ? (uint8_t)c : (uint8_t)4;
@@ -111,6 +158,17 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             const uint32_t q = i / 5u, col = i - q * 5u;
             tab5[i] = col < 4 ? p.one[q * 4u + col] : p.reset_entry;
         }
+    if (ptab_in_smem)
+        for (uint32_t i = tid; i < p.n_states * 16u; i += nthr) {
+            // pair index: first code in bits 0..1, second in bits 2..3 (code = (byte >> 1) & 3)
+            const uint32_t q = i >> 4;
+            const uint32_t e1 = p.one[q * 4u + (i & 3u)];
+            const uint32_t e2 = p.one[(e1 & 0x7FFFFFFFu) * 4u + ((i >> 2) & 3u)];
+            ptab[i] = (e2 & 0x3FFFFFFFu) | ((e1 >> 31) << 30) | ((e2 >> 31) << 31);
+        }
+    // everything above reads only the automaton; the scan's results are read below, after
+    // the scan grid has completed (a no-op when not launched as a programmatic dependent)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint64_t c = (uint64_t)blockIdx.x * nthr + tid;
     const bool act = c < p.nseg;
     const unsigned long long v = act ? p.count[c] : 0u;
@@ -221,6 +279,8 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             const uint64_t rs = b + (uint64_t)rec[0] * kTile;
             uint32_t k0, k1;
             row_span(rs, rs > p.lo ? rs : p.lo, rs + kTile < cend ? rs + kTile : cend, k0, k1);
+            if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile && walk_row_pairs(p, ptab, rs, rec[1], o))
+                continue;
             walk_row(slot, rs, k0, k1, rec[1], o);
         }
     }
@@ -442,9 +502,10 @@ int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Pl
 
 // device scratch carved from one stream-ordered allocation
 struct Scratch {
-    uint32_t *spec_start, *last_state, *count, *nrec, *stash, *pending, *pending_a, *div_list, *ctrl;
+    uint32_t *spec_start, *last_state, *count, *nrec, *stash, *pending, *div_list, *ctrl;
     uint8_t *flags;
     unsigned long long *cta_sum, *cta_off;
+    uint4 *block_head;
     size_t bytes;
 };
 
@@ -456,12 +517,12 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
     s.ctrl = (uint32_t *)take(16);
     s.cta_sum = (unsigned long long *)take(nblocks * 8);
     s.cta_off = (unsigned long long *)take(nblocks * 8);
+    s.block_head = (uint4 *)take(nblocks * 16);
     s.spec_start = (uint32_t *)take(nseg * 4);
     s.last_state = (uint32_t *)take(nseg * 4);
     s.count = (uint32_t *)take(nseg * 4);
     s.flags = (uint8_t *)take(nseg);
     s.pending = (uint32_t *)take((size_t)pending_cap * 4);
-    s.pending_a = (uint32_t *)take((size_t)pending_cap * 4);
     s.div_list = (uint32_t *)take((size_t)div_cap * 4);
     s.stash = positions ? (uint32_t *)take(nseg * kStashCap * 12) : nullptr;
     s.nrec = positions ? (uint32_t *)take(nseg * 4) : nullptr;
@@ -508,9 +569,9 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
     sp.stash = s.stash; sp.nrec = s.nrec; sp.flags = s.flags;
     sp.prefetch_tiles = pl.prefetch;
-    sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap; sp.pending_a = s.pending_a;
+    sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
-    sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.out_count = out_count;
+    sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
     sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
     sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
 
@@ -527,21 +588,35 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         ep.one = d->d_one; ep.reset_entry = d->reset_entry; ep.n_states = d->n_states;
         ep.last_state = s.last_state; ep.count = s.count; ep.stash = s.stash; ep.nrec = s.nrec;
         ep.flags = s.flags; ep.cta_off = s.cta_off; ep.out = out_positions; ep.cap = cap;
+        ep.lut_lo = 0x00630061u; ep.lut_hi = 0x00670074u;
         const uint32_t cpb = (uint32_t)pl.warps * 32u;   // one extraction thread per chunk
         const uint32_t tab5_smem = d->n_states * 5u <= 4096u ? 1u : 0u;
+        const uint32_t ptab_smem = d->n_states <= 1024u ? 1u : 0u;   // 64 B per state
         const size_t esmem = (size_t)kEmitWalkers * kEmitRowPitch + (size_t)cpb * 8 + (size_t)(cpb + 1) * 4 +
-                             (tab5_smem ? (size_t)d->n_states * 20 : 0);
+                             (tab5_smem ? (size_t)d->n_states * 20 : 0) + (ptab_smem ? (size_t)d->n_states * 64 : 0);
         const size_t optin = device_props(d->device).smem_optin;
         // the extraction kernel's static shared memory is about 10 KB; 16 KB is reserved
         int rc2 = ensure_smem_optin((const void *)emit_kernel, d->device, (optin ? optin : 232448) - 16384);
         if (rc2) e = cudaErrorInvalidValue;
         else {
             const ProfToken et = prof_begin(stream);
-            emit_kernel<<<pl.grid, cpb, esmem, stream>>>(ep, tab5_smem);
+            // programmatic dependent launch: the extraction grid is scheduled while the
+            // scan's last block joins, and waits (griddepcontrol.wait) for its results
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)pl.grid);
+            cfg.blockDim = dim3(cpb);
+            cfg.dynamicSmemBytes = esmem;
+            cfg.stream = stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = et.a ? 0 : 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, emit_kernel, ep, tab5_smem, ptab_smem);
+            if (e == cudaSuccess) e = cudaGetLastError();
             prof_end(et, stream, PROF_EMIT);
+            record_launch();
         }
-        e = cudaGetLastError();
-        record_launch();
     }
     cudaError_t e2 = cudaFreeAsync(mem, stream);
     if (e == cudaSuccess) e = e2;
@@ -752,9 +827,9 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
     sp.stash = nullptr; sp.nrec = nullptr; sp.flags = s.flags;
     sp.prefetch_tiles = pl.prefetch;
-    sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap; sp.pending_a = s.pending_a;
+    sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
-    sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.out_count = out_count;
+    sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
     sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
     sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
     scan_fn(pl.mode, pl.warps, false)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);

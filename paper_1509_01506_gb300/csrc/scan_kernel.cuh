@@ -41,13 +41,13 @@ struct ScanParams {
     uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
     uint8_t *flags;         // [nseg] 1 = extraction must rescan the chunk from its true start
     uint32_t *ctrl;         // [4] zeroed before launch: finish ticket, pending, diverged, 0
-    uint32_t *pending;      // chunks the last block must repair (first chunk of each block,
-    uint32_t pending_cap;   //   and chunks whose 16-byte repair did not converge)
-    uint32_t *pending_a;    // [pending_cap] snapshot of each pending chunk's true start
+    uint32_t *pending;      // chunks whose 16-byte in-block repair did not converge (the last
+    uint32_t pending_cap;   //   block repairs them; it joins every block's first chunk anyway)
     uint32_t *div_list;     // [div_cap] chunks whose last state changed in a repair
     uint32_t div_cap;
     unsigned long long *cta_sum;   // [grid] count of each block's chunks
     unsigned long long *cta_off;   // [grid] exclusive prefix of cta_sum (for extraction)
+    uint4 *block_head;             // [grid] first 16 bytes of each block's first chunk
     uint64_t *out_count;
     // 1, 2^16, 2^5, 2^28 passed at run time so the compiler keeps the multiplies that
     // use them (adds and shifts) on the FMA pipe instead of turning them into ALU ops
@@ -149,20 +149,33 @@ __device__ __forceinline__ uint32_t row_bytes_global(const OneTable &T, uint32_t
 // (count, last state, records) to be those of the run from 's'.
 struct Repair { uint32_t count, last; uint8_t flag; };
 
-__device__ Repair repair_chunk(const ScanParams &p, uint64_t c, uint32_t a, uint32_t s) {
+__device__ Repair repair_chunk(const ScanParams &p, const OneTable &T, uint64_t c, uint32_t a, uint32_t s,
+                              const uint4 *head) {
     const uint64_t b = c * p.seg_bytes;
     const uint64_t from = b > p.lo ? b : p.lo;
     const uint64_t to = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
     uint32_t qa = a, qs = s, ca = 0, cs = 0;
     uint64_t met_at = ~0ull;
-    walk_range(p.abase, from, to, p.hi, [&](uint64_t off, uint32_t byte) {
-        const uint32_t ea = one_step(p.one, p.reset_entry, qa, byte);
-        const uint32_t es = one_step(p.one, p.reset_entry, qs, byte);
+    auto step = [&](uint64_t off, uint32_t byte) {
+        const uint32_t ea = T.step(qa, byte);
+        const uint32_t es = T.step(qs, byte);
         qa = ea & 0x7FFFFFFFu; qs = es & 0x7FFFFFFFu;
         ca += ea >> 31; cs += es >> 31;
         if (qa == qs) { met_at = off; return false; }
         return true;
-    });
+    };
+    uint64_t resume = from;
+    if (head) {
+        // the chunk's first 16 bytes, saved by its block: the runs almost always meet here
+        const uint32_t hw[4] = {head->x, head->y, head->z, head->w};
+        for (int k = 0; k < 16; ++k) {
+            const uint64_t off = b + (uint64_t)k;
+            if (off < from) continue;
+            if (off >= to || !step(off, (hw[k >> 2] >> (8 * (k & 3))) & 0xFFu)) break;
+        }
+        resume = b + 16;
+    }
+    if (met_at == ~0ull && resume < to) walk_range(p.abase, resume, to, p.hi, step);
     Repair r;
     if (met_at != ~0ull) {
         r.count = p.count[c] - cs + ca;
@@ -188,45 +201,57 @@ __device__ Repair repair_chunk(const ScanParams &p, uint64_t c, uint32_t a, uint
 // Makes chunk c's results those of the run from its true start a: count (and its block
 // sum), assumed start, last state, flags.
 __device__ __forceinline__ void apply_repair(const ScanParams &p, uint64_t c, uint32_t a,
-                                             const Repair &r, uint32_t chunks_per_block) {
+                                             const Repair &r, uint32_t chunks_per_block,
+                                             unsigned long long *sums) {
     const uint32_t old = p.count[c];
     p.count[c] = r.count;
-    atomicAdd(&p.cta_sum[c / chunks_per_block], (unsigned long long)(long long)((int64_t)r.count - (int64_t)old));
+    atomicAdd(&sums[c / chunks_per_block], (unsigned long long)(long long)((int64_t)r.count - (int64_t)old));
     p.spec_start[c] = a;
     p.last_state[c] = r.last;
     if (r.flag) p.flags[c] = 1;
 }
 
 // The join across blocks (Sec. III-A "binary reduction"), run by the last block to
-// finish: repairs the pending chunks in parallel (each from the last state of the chunk
-// before it, as it stood when the blocks finished), then walks forward from every chunk
-// whose last state changed until the chain agrees again, then writes the total count and
-// each block's output offset. Every chunk's (assumed start, count, last state) triple
-// stays consistent throughout.
+// finish. Each chunk's true start is the last state of the chunk before it. The first
+// chunk of every block and the chunks whose in-block repair did not meet within 16
+// bytes are repaired in parallel (Sec. III-B.3); every repair leaves a consistent
+// (assumed start, count, last state) triple, so a chunk whose last state changed is
+// followed forward until the next chunk's assumed start equals the true last state
+// before it (the cascade). Then the block sums are scanned into output offsets and the
+// total is written. 's_sum' is shared memory for the block sums (the staging area, idle
+// by now) or null, in which case they are updated in global memory.
 template <int THREADS>
-__device__ void finalize_block(const ScanParams &p) {
+__device__ void finalize_block(const ScanParams &p, const OneTable &T, unsigned long long *s_sum) {
     __shared__ unsigned long long wsum[THREADS / 32];
     __shared__ unsigned long long carry;
     const uint32_t tid = threadIdx.x;
     const uint32_t cpb = THREADS;   // chunks per scan block
+    const uint32_t nb = gridDim.x;
+    unsigned long long *sums = s_sum ? s_sum : p.cta_sum;
+    if (s_sum)
+        for (uint32_t i = tid; i < nb; i += THREADS) s_sum[i] = p.cta_sum[i];
     const uint32_t np = p.ctrl[1];
-    if (np <= p.pending_cap) {
-        for (uint32_t i = tid; i < np; i += THREADS) p.pending_a[i] = p.last_state[p.pending[i] - 1];
-        __syncthreads();
-        for (uint32_t i = tid; i < np; i += THREADS) {
-            const uint64_t c = p.pending[i];
-            const uint32_t a = p.pending_a[i];
-            const uint32_t s = p.spec_start[c];
-            if (a == s) continue;
-            const uint32_t old_last = p.last_state[c];
-            const Repair r = repair_chunk(p, c, a, s);
-            apply_repair(p, c, a, r, cpb);
-            if (r.last != old_last) {
-                const uint32_t k = atomicAdd(&p.ctrl[2], 1u);
-                if (k < p.div_cap) p.div_list[k] = (uint32_t)c;
-            }
+    __syncthreads();
+    auto repair_one = [&](uint64_t c, const uint4 *head) {
+        const uint32_t a = p.last_state[c - 1];
+        const uint32_t s = p.spec_start[c];
+        if (a == s) return;
+        const uint32_t old_last = p.last_state[c];
+        const Repair r = repair_chunk(p, T, c, a, s, head);
+        apply_repair(p, c, a, r, cpb, sums);
+        if (r.last != old_last) {
+            const uint32_t k = atomicAdd(&p.ctrl[2], 1u);
+            if (k < p.div_cap) p.div_list[k] = (uint32_t)c;
         }
+    };
+    // the first chunk of every block but the first, with its saved first 16 bytes
+    for (uint32_t b = tid + 1; b < nb; b += THREADS) {
+        const uint64_t c = (uint64_t)b * cpb;
+        if (c < p.nseg) repair_one(c, &p.block_head[b]);
     }
+    // chunks whose in-block repair did not converge
+    if (np <= p.pending_cap)
+        for (uint32_t i = tid; i < np; i += THREADS) repair_one(p.pending[i], nullptr);
     __syncthreads();
     if (tid == 0) {
         const uint32_t nd = p.ctrl[2];
@@ -236,8 +261,8 @@ __device__ void finalize_block(const ScanParams &p) {
                 const uint32_t a = p.last_state[c - 1];
                 const uint32_t s = p.spec_start[c];
                 if (a == s) continue;
-                const Repair r = repair_chunk(p, c, a, s);
-                apply_repair(p, c, a, r, cpb);
+                const Repair r = repair_chunk(p, T, c, a, s, nullptr);
+                apply_repair(p, c, a, r, cpb, sums);
             }
         } else if (nd > 0) {
             // sort the (small) list of chunks whose last state changed, then walk forward
@@ -257,8 +282,8 @@ __device__ void finalize_block(const ScanParams &p) {
                 uint64_t k = c + 1;
                 for (;;) {
                     if (k >= p.nseg || cur == p.spec_start[k]) { walked = k; break; }
-                    const Repair r = repair_chunk(p, k, cur, p.spec_start[k]);
-                    apply_repair(p, k, cur, r, cpb);
+                    const Repair r = repair_chunk(p, T, k, cur, p.spec_start[k], nullptr);
+                    apply_repair(p, k, cur, r, cpb, sums);
                     p.flags[k] = 1;   // its records follow a start that was not the true one
                     cur = r.last;
                     ++k;
@@ -269,10 +294,9 @@ __device__ void finalize_block(const ScanParams &p) {
     }
     __syncthreads();
     // exclusive scan of the block sums -> output offsets; total -> out_count
-    const uint32_t nb = gridDim.x;
     for (uint32_t base = 0; base < nb; base += THREADS) {
         const uint32_t i = base + tid;
-        const unsigned long long v = i < nb ? p.cta_sum[i] : 0ull;
+        const unsigned long long v = i < nb ? sums[i] : 0ull;
         unsigned long long x = v;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
@@ -453,7 +477,10 @@ scan_kernel(ScanParams p) {
         if (t + 1 < ntiles) issue(t + 1);
         cp_async_commit();
         if (p.prefetch_tiles) prefetch(t + 1 + p.prefetch_tiles);
-        if (t == 0) head_s[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+        if (t == 0) {
+            head_s[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+            if (threadIdx.x == 0) p.block_head[blockIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
         if (!live) continue;
 
         if (MODE == MODE_PAIR) {
@@ -521,7 +548,7 @@ scan_kernel(ScanParams p) {
     uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, last, 1);
     if (lane == 0) prev = warp > 0 ? warp_last[warp - 1] : 0u;
     const bool has_prev = active && seg > 0 && (lane > 0 || warp > 0);
-    bool pending = active && seg > 0 && !has_prev;   // first chunk of the block
+    bool pending = false;   // a block's first chunk is joined by the last block directly
     if (has_prev && prev != spec) {
         // run the true start and the speculated start in lockstep over the chunk's first
         // bytes; at the first step where their states are equal, the rest of the chunk is
@@ -563,6 +590,9 @@ scan_kernel(ScanParams p) {
         if (k < p.pending_cap) p.pending[k] = (uint32_t)seg;
     }
     __threadfence();   // this thread's results are visible before the block's ticket
+    // the extraction kernel (launched as a programmatic dependent) may be scheduled once
+    // every block has got here; it still waits for this grid to finish before reading
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // block sum of the chunk counts
     unsigned long long v = active ? cnt : 0u;
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
@@ -580,7 +610,10 @@ scan_kernel(ScanParams p) {
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    finalize_block<WARPS * 32>(p);
+    // the staging area is idle now: it holds the block sums while the last block joins
+    unsigned long long *s_sum = gridDim.x * 8u <= (uint32_t)WARPS * kStageBytes
+                                    ? reinterpret_cast<unsigned long long *>(smem) : nullptr;
+    finalize_block<WARPS * 32>(p, T, s_sum);
 }
 
 }  // namespace
