@@ -92,45 +92,64 @@ __device__ __forceinline__ void stage_row(uint8_t *slot, const uint8_t *abase, u
 // (A, C, T, G -> code, anything else -> 4) and a five-column transition table whose fifth
 // column is the reset symbol.
 // Walks one whole 128-byte row of bases with the two-symbol table 'ptab' (entry: next
-// state | accept after the first symbol << 30 | accept after the second << 31), writing
-// the accepting positions from output index o. Returns false (and writes nothing) when
-// some byte of the row is not a base; the caller then walks it byte by byte.
+// state | accept after the first symbol << 30 | accept after the second << 31) and
+// writes the accepting positions from output index o. The walk itself has no branches:
+// the accept bits of the 128 positions collect in a 4-word mask, which is turned into
+// positions afterwards. Unless 'checked', the row is first tested for non-base bytes;
+// then it returns false (writing nothing) and the caller walks the row byte by byte.
 __device__ __forceinline__ bool walk_row_pairs(const EmitParams &p, const uint32_t *ptab, uint64_t rs,
-                                               uint32_t q, unsigned long long o) {
+                                               uint32_t q, unsigned long long o, bool checked) {
     const uint4 *src = reinterpret_cast<const uint4 *>(p.abase + rs);
-    uint32_t err = 0;
+    if (!checked) {
+        uint32_t err = 0;
 #pragma unroll
-    for (int h = 0; h < 8; ++h) {   // check first: no position is written for a mixed row
-        const uint4 v = src[h];
-        const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+        for (int h = 0; h < 8; ++h) {
+            const uint4 v = src[h];
+            const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t x = ww[i] & 0x06060606u;
-            const uint32_t z = x | (x >> 4);
-            err |= __byte_perm(p.lut_lo, p.lut_hi, __byte_perm(z, 0, 0x0020)) ^ ww[i];
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t x = ww[i] & 0x06060606u;
+                const uint32_t z = x | (x >> 4);
+                err |= __byte_perm(p.lut_lo, p.lut_hi, __byte_perm(z, 0, 0x0020)) ^ ww[i];
+            }
         }
+        if (err & 0xDFDFDFDFu) return false;
     }
-    if (err & 0xDFDFDFDFu) return false;
-    const uint64_t pos0 = rs - p.lo;
-#pragma unroll 1
+    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(ptab);
+    uint32_t m[4];
+#pragma unroll
     for (int half = 0; half < 2; ++half) {
         uint4 v[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) v[h] = src[4 * half + h];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const uint32_t w = i % 4 == 0 ? v[i / 4].x : i % 4 == 1 ? v[i / 4].y : i % 4 == 2 ? v[i / 4].z : v[i / 4].w;
-            const uint32_t y = (w & 0x06060606u) * 65u;   // pair codes at bits 7..10 and 23..26
-            const uint64_t pw = pos0 + 64u * half + 4u * i;
+        for (int mw = 0; mw < 2; ++mw) {          // one mask word: 32 positions = 8 words
+            uint32_t bits = 0;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const uint32_t e = ptab[q * 16u + ((y >> (j ? 23 : 7)) & 15u)];
-                q = e & 0x3FFFFFFFu;
-                if (e >> 30) {
-                    if (e & (1u << 30)) { if (o < p.cap) p.out[o] = pw + 2u * j; ++o; }
-                    if (e >> 31) { if (o < p.cap) p.out[o] = pw + 2u * j + 1u; ++o; }
+            for (int i = 0; i < 8; ++i) {
+                const int wi = 8 * mw + i;        // word within this half
+                const uint32_t w = wi % 4 == 0 ? v[wi / 4].x : wi % 4 == 1 ? v[wi / 4].y
+                                 : wi % 4 == 2 ? v[wi / 4].z : v[wi / 4].w;
+                const uint32_t y = (w & 0x06060606u) * 65u;   // pair codes at bits 7..10, 23..26
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t e = lds_u32(pbase + (q * 16u + ((y >> (j ? 23 : 7)) & 15u)) * 4u);
+                    q = e & 0x3FFFFFFFu;
+                    bits |= (e >> 30) << (4 * i + 2 * j);
                 }
             }
+            m[2 * half + mw] = bits;
+        }
+    }
+    const uint64_t pos0 = rs - p.lo;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t bits = m[k];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            if (o < p.cap) p.out[o] = pos0 + 32u * k + (uint32_t)b;
+            ++o;
+            bits &= bits - 1;
         }
     }
     return true;
@@ -276,10 +295,12 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             if (o >= p.cap) continue;
             const uint64_t b = cj * S;
             const uint64_t cend = b + S < p.hi ? b + S : p.hi;
-            const uint64_t rs = b + (uint64_t)rec[0] * kTile;
+            const bool all_bases = (rec[0] & kRowAllBases) != 0;
+            const uint64_t rs = b + (uint64_t)(rec[0] & ~kRowAllBases) * kTile;
             uint32_t k0, k1;
             row_span(rs, rs > p.lo ? rs : p.lo, rs + kTile < cend ? rs + kTile : cend, k0, k1);
-            if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile && walk_row_pairs(p, ptab, rs, rec[1], o))
+            if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile &&
+                walk_row_pairs(p, ptab, rs, rec[1], o, all_bases))
                 continue;
             walk_row(slot, rs, k0, k1, rec[1], o);
         }

@@ -16,6 +16,9 @@ namespace dnalib {
 constexpr int kStages = 1;          // one stage per warp: rows are copied to registers first
 constexpr int kStageBytes = 32 * kTile;
 constexpr int kStashCap = 8;        // hit-row records kept per chunk before a rescan
+// set in a hit-row record's tile field when the scan saw the whole row and every byte of
+// it was a base (the extraction then walks it two symbols at a time without checking)
+constexpr uint32_t kRowAllBases = 0x80000000u;
 constexpr uint32_t kMaxLookback = 64;
 constexpr uint32_t kMaxStates = 1u << 24;
 constexpr uint32_t kDefaultPrefetch = 0;  // tiles of L2 prefetch ahead of the stage
@@ -110,7 +113,7 @@ __device__ __forceinline__ void fix_hit_rows(uint32_t *stash, uint32_t &nrec, ui
     const uint32_t n = nrec < (uint32_t)kStashCap ? nrec : (uint32_t)kStashCap;
     bool row0 = false;
     for (uint32_t r = 0; r < n; ++r) {
-        if (stash[3 * r] == 0) { stash[3 * r + 1] = q_true; row0 = true; }
+        if ((stash[3 * r] & ~kRowAllBases) == 0) { stash[3 * r + 1] = q_true; row0 = true; }
         else stash[3 * r + 2] += delta;
     }
     if (!row0 && pa > 0) {
@@ -511,7 +514,7 @@ scan_kernel(ScanParams p) {
                 }
                 if ((err & 0xDFDFDFDFu) == 0) {
                     if (POS && rc)
-                        record_hit_row(stash, nrec, t,
+                        record_hit_row(stash, nrec, t | kRowAllBases,
                                        ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes, cnt);
                     cnt += rc;
                     cur = c2 & 0x3FFFFu;
