@@ -58,7 +58,7 @@ struct EmitParams {
     uint64_t lo, hi, seg_bytes, nseg;
     const uint32_t *one;
     uint32_t reset_entry, n_states;
-    const uint32_t *last_state, *count, *stash, *nrec;
+    const uint32_t *last_state, *count, *stash, *nrec, *spec_start, *fix_delta;
     const uint8_t *flags;
     const unsigned long long *cta_off;
     uint64_t *out;
@@ -155,6 +155,23 @@ __device__ __forceinline__ bool walk_row_pairs(const EmitParams &p, const uint32
     return true;
 }
 
+// Record i of chunk c as the true run's: records are written by the speculative run; a
+// chunk repaired at its converging point inside row 0 (kFlagFixed) takes its row-0 start
+// from the true start and moves later rows' count offsets by its delta, and when the
+// true run accepts before the meeting point but the speculative run recorded no row 0,
+// a row-0 record is inserted in front (ins = 1).
+__device__ __forceinline__ uint3 chunk_record(const EmitParams &p, uint64_t c, uint32_t i, bool fixed,
+                                              uint32_t ins, uint32_t delta, uint32_t row0) {
+    if (ins && i == 0) return make_uint3(0u, row0, 0u);
+    const uint32_t *g = p.stash + c * (kStashCap * 3) + 3 * (i - ins);
+    uint3 r = make_uint3(g[0], g[1], g[2]);
+    if (fixed) {
+        if ((r.x & ~kRowAllBases) == 0) r.y = row0;
+        else r.z += delta;
+    }
+    return r;
+}
+
 __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_in_smem, uint32_t ptab_in_smem) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ unsigned long long wsum[32];
@@ -163,9 +180,11 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     __shared__ uint8_t s_rescan[1024];
     __shared__ uint4 s_rec[kEmitRecs];   // (tile, start state, count before, chunk index)
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    // dynamic shared memory: [row slots: walkers x pitch][offsets: nthr x 8][slots: nthr+1 x 4][table]
+    // dynamic shared memory: [row slots: walkers x pitch][offsets: nthr x 8][fix: nthr x 8]
+    //                        [slots: nthr+1 x 4][tables]
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(dsm + kEmitWalkers * kEmitRowPitch);
-    uint32_t *s_slot = reinterpret_cast<uint32_t *>(s_off + nthr);
+    uint2 *s_fix = reinterpret_cast<uint2 *>(s_off + nthr);
+    uint32_t *s_slot = reinterpret_cast<uint32_t *>(s_fix + nthr);
     uint32_t *tab5 = s_slot + nthr + 1;
     uint32_t *ptab = tab5 + (tab5_in_smem ? p.n_states * 5u : 0u);
     if (tid < 256) {
@@ -192,8 +211,14 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     const bool act = c < p.nseg;
     const unsigned long long v = act ? p.count[c] : 0u;
     const uint32_t nr = act ? p.nrec[c] : 0u;
-    const bool rescan = act && v > 0 && (p.flags[c] != 0 || nr > (uint32_t)kStashCap);
-    const uint32_t rows = (act && !rescan) ? nr : 0u;
+    const uint8_t fl = act ? p.flags[c] : 0;
+    const bool fixed = (fl & kFlagFixed) != 0;
+    const uint32_t ins = fixed && !(fl & kFlagRow0Rec) && (fl & kFlagPrefixHit) ? 1u : 0u;
+    const bool rescan = act && v > 0 && ((fl & kFlagRescan) != 0 || nr + ins > (uint32_t)kStashCap);
+    // a chunk without matches has no rows to walk, whatever its speculative run recorded
+    const uint32_t rows = (act && v > 0 && !rescan) ? nr + ins : 0u;
+    uint2 fix = make_uint2(0u, 0u);
+    if (fixed && rows) fix = make_uint2(p.fix_delta[c], p.spec_start[c]);
     unsigned long long x = v;
     uint32_t y = rows;
     for (int o = 1; o < 32; o <<= 1) {
@@ -221,13 +246,14 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     s_off[tid] = off;
     s_slot[tid] = by + y - rows;
     if (tid == nthr - 1) s_slot[nthr] = by + y;
-    s_rescan[tid] = rescan ? 1 : 0;
+    s_rescan[tid] = (rescan ? 1 : 0) | (fixed ? 2 : 0) | (ins ? 4 : 0);
+    s_fix[tid] = fix;
     // each chunk copies its hit-row records into shared memory (first kEmitRecs rows)
     const uint32_t slot0 = by + y - rows;
     for (uint32_t i = 0; i < rows; ++i) {
         if (slot0 + i >= (uint32_t)kEmitRecs) break;
-        const uint32_t *rec = p.stash + c * (kStashCap * 3) + 3 * i;
-        s_rec[slot0 + i] = make_uint4(rec[0], rec[1], rec[2], (uint32_t)tid);
+        const uint3 r = chunk_record(p, c, i, fixed, ins, fix.x, fix.y);
+        s_rec[slot0 + i] = make_uint4(r.x, r.y, r.z, (uint32_t)tid);
     }
     __syncthreads();
     const uint32_t total_rows = s_slot[nthr];
@@ -258,7 +284,7 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     if (tid < kEmitWalkers) {
         uint8_t *slot = dsm + tid * kEmitRowPitch;
         for (uint32_t j = tid; j < nthr; j += kEmitWalkers) {
-            if (!s_rescan[j]) continue;
+            if (!(s_rescan[j] & 1)) continue;
             const uint64_t cj = (uint64_t)blockIdx.x * nthr + j;
             const unsigned long long oj = s_off[j];
             if (oj >= p.cap) continue;
@@ -287,8 +313,10 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
                     if (s_slot[mid] <= r) lo = mid; else hi = mid - 1;
                 }
                 const uint64_t cl = (uint64_t)blockIdx.x * nthr + lo;
-                const uint32_t *g = p.stash + cl * (kStashCap * 3) + 3 * (r - s_slot[lo]);
-                rec[0] = g[0]; rec[1] = g[1]; rec[2] = g[2];
+                const uint8_t bits = s_rescan[lo];
+                const uint3 g = chunk_record(p, cl, r - s_slot[lo], (bits & 2) != 0, (bits >> 2) & 1u,
+                                             s_fix[lo].x, s_fix[lo].y);
+                rec[0] = g.x; rec[1] = g.y; rec[2] = g.z;
             }
             const uint64_t cj = (uint64_t)blockIdx.x * nthr + lo;
             unsigned long long o = s_off[lo] + rec[2];
@@ -523,7 +551,7 @@ int make_plan(const dna_dfa *d, uint64_t total, bool pos, const dna_plan *ov, Pl
 
 // device scratch carved from one stream-ordered allocation
 struct Scratch {
-    uint32_t *spec_start, *last_state, *count, *nrec, *stash, *pending, *div_list, *ctrl;
+    uint32_t *spec_start, *last_state, *count, *nrec, *stash, *fix_delta, *pending, *div_list, *ctrl;
     uint8_t *flags;
     unsigned long long *cta_sum, *cta_off;
     uint4 *block_head;
@@ -547,6 +575,7 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
     s.div_list = (uint32_t *)take((size_t)div_cap * 4);
     s.stash = positions ? (uint32_t *)take(nseg * kStashCap * 12) : nullptr;
     s.nrec = positions ? (uint32_t *)take(nseg * 4) : nullptr;
+    s.fix_delta = positions ? (uint32_t *)take(nseg * 4) : nullptr;
     s.bytes = off;
 }
 
@@ -588,7 +617,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     sp.lookback = pl.lookback; sp.n_states = d->n_states; sp.reset_entry = d->reset_entry;
     sp.one = d->d_one; sp.pair = d->d_pair;
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
-    sp.stash = s.stash; sp.nrec = s.nrec; sp.flags = s.flags;
+    sp.stash = s.stash; sp.nrec = s.nrec; sp.flags = s.flags; sp.fix_delta = s.fix_delta;
     sp.prefetch_tiles = pl.prefetch;
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
@@ -608,12 +637,13 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         ep.abase = abase; ep.lo = shift; ep.hi = total; ep.seg_bytes = pl.seg_bytes; ep.nseg = pl.nseg;
         ep.one = d->d_one; ep.reset_entry = d->reset_entry; ep.n_states = d->n_states;
         ep.last_state = s.last_state; ep.count = s.count; ep.stash = s.stash; ep.nrec = s.nrec;
+        ep.spec_start = s.spec_start; ep.fix_delta = s.fix_delta;
         ep.flags = s.flags; ep.cta_off = s.cta_off; ep.out = out_positions; ep.cap = cap;
         ep.lut_lo = 0x00630061u; ep.lut_hi = 0x00670074u;
         const uint32_t cpb = (uint32_t)pl.warps * 32u;   // one extraction thread per chunk
         const uint32_t tab5_smem = d->n_states * 5u <= 4096u ? 1u : 0u;
         const uint32_t ptab_smem = d->n_states <= 1024u ? 1u : 0u;   // 64 B per state
-        const size_t esmem = (size_t)kEmitWalkers * kEmitRowPitch + (size_t)cpb * 8 + (size_t)(cpb + 1) * 4 +
+        const size_t esmem = (size_t)kEmitWalkers * kEmitRowPitch + (size_t)cpb * 16 + (size_t)(cpb + 1) * 4 +
                              (tab5_smem ? (size_t)d->n_states * 20 : 0) + (ptab_smem ? (size_t)d->n_states * 64 : 0);
         const size_t optin = device_props(d->device).smem_optin;
         // the extraction kernel's static shared memory is about 10 KB; 16 KB is reserved
@@ -846,7 +876,7 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     sp.lookback = pl.lookback; sp.n_states = d->n_states; sp.reset_entry = d->reset_entry;
     sp.one = d->d_one; sp.pair = d->d_pair;
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
-    sp.stash = nullptr; sp.nrec = nullptr; sp.flags = s.flags;
+    sp.stash = nullptr; sp.nrec = nullptr; sp.flags = s.flags; sp.fix_delta = nullptr;
     sp.prefetch_tiles = pl.prefetch;
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.div_list = s.div_list; sp.div_cap = div_cap;

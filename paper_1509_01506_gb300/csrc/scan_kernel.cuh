@@ -42,7 +42,8 @@ struct ScanParams {
     uint32_t *stash;        // [nseg][kStashCap][3] hit rows {tile, start state, count before}, or null
     uint32_t prefetch_tiles; // L2 prefetch distance in tiles (0 = off)
     uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
-    uint8_t *flags;         // [nseg] 1 = extraction must rescan the chunk from its true start
+    uint8_t *flags;         // [nseg] kFlag* bits for the extraction pass
+    uint32_t *fix_delta;    // [nseg] count offset shift of a kFlagFixed chunk's later rows
     uint32_t *ctrl;         // [4] zeroed before launch: finish ticket, pending, diverged, 0
     uint32_t *pending;      // chunks whose 16-byte in-block repair did not converge (the last
     uint32_t pending_cap;   //   block repairs them; it joins every block's first chunk anyway)
@@ -101,33 +102,13 @@ __device__ __forceinline__ void record_hit_row(uint32_t *stash, uint32_t &nrec, 
     ++nrec;
 }
 
-// After a chunk's speculative run was repaired at its converging point (the true start
-// and the speculated start met within the chunk's first row), the hit-row records of the
-// speculative run are made those of the true run: row 0 is re-walked from the true start,
-// later rows keep their start states (the runs coincide there) and shift their count
-// offsets by delta = true prefix count - speculative prefix count. 'pa' is the true run's
-// count over the prefix; if the true prefix has accepting steps but row 0 had no record,
-// a record for row 0 is inserted in front.
-__device__ __forceinline__ void fix_hit_rows(uint32_t *stash, uint32_t &nrec, uint32_t q_true,
-                                             uint32_t delta, uint32_t pa) {
-    const uint32_t n = nrec < (uint32_t)kStashCap ? nrec : (uint32_t)kStashCap;
-    bool row0 = false;
-    for (uint32_t r = 0; r < n; ++r) {
-        if ((stash[3 * r] & ~kRowAllBases) == 0) { stash[3 * r + 1] = q_true; row0 = true; }
-        else stash[3 * r + 2] += delta;
-    }
-    if (!row0 && pa > 0) {
-        if (nrec < (uint32_t)kStashCap) {
-            for (uint32_t r = n; r > 0; --r) {
-                stash[3 * r] = stash[3 * (r - 1)];
-                stash[3 * r + 1] = stash[3 * (r - 1) + 1];
-                stash[3 * r + 2] = stash[3 * (r - 1) + 2];
-            }
-            stash[0] = 0; stash[1] = q_true; stash[2] = 0;
-        }
-        ++nrec;   // beyond the capacity: the extraction pass rescans the chunk
-    }
-}
+// Chunk flag bits (ScanParams::flags), read by the extraction pass.
+constexpr uint8_t kFlagRescan = 1;    // extract by rescanning the chunk from its true start
+constexpr uint8_t kFlagFixed = 2;     // the speculative run met the true run inside row 0:
+                                      // row 0 starts from the true start (spec_start) and
+                                      // later rows' count offsets move by fix_delta
+constexpr uint8_t kFlagRow0Rec = 4;   // the speculative run recorded row 0
+constexpr uint8_t kFlagPrefixHit = 8; // the true run accepts before the meeting point
 
 // Per-byte walk over aligned offsets [from, to) read from global memory: rows with a
 // reset byte, the first row of an unaligned sequence and the last row of the last chunk.
@@ -150,13 +131,16 @@ __device__ __forceinline__ uint32_t row_bytes_global(const OneTable &T, uint32_t
 // Hit-row records are fixed when the runs meet inside row 0; otherwise the chunk is
 // flagged for a rescan by the extraction pass. Requires the chunk's current results
 // (count, last state, records) to be those of the run from 's'.
-struct Repair { uint32_t count, last; uint8_t flag; };
+struct Repair { uint32_t count, last, old_count, delta; uint8_t flag; };
 
 __device__ Repair repair_chunk(const ScanParams &p, const OneTable &T, uint64_t c, uint32_t a, uint32_t s,
                               const uint4 *head) {
     const uint64_t b = c * p.seg_bytes;
     const uint64_t from = b > p.lo ? b : p.lo;
     const uint64_t to = b + p.seg_bytes < p.hi ? b + p.seg_bytes : p.hi;
+    // the chunk's current results, loaded up front so they overlap the walk
+    const uint32_t cur_count = p.count[c], cur_last = p.last_state[c];
+    const uint8_t cur_flags = p.stash ? p.flags[c] : 0;
     uint32_t qa = a, qs = s, ca = 0, cs = 0;
     uint64_t met_at = ~0ull;
     auto step = [&](uint64_t off, uint32_t byte) {
@@ -180,23 +164,23 @@ __device__ Repair repair_chunk(const ScanParams &p, const OneTable &T, uint64_t 
     }
     if (met_at == ~0ull && resume < to) walk_range(p.abase, resume, to, p.hi, step);
     Repair r;
+    r.old_count = cur_count;
+    r.delta = 0;
     if (met_at != ~0ull) {
-        r.count = p.count[c] - cs + ca;
-        r.last = p.last_state[c];
+        r.count = cur_count - cs + ca;
+        r.last = cur_last;
         r.flag = 0;
         if (p.stash) {
-            if (met_at < b + kTile) {
-                uint32_t nr = p.nrec[c];
-                fix_hit_rows(p.stash + c * (kStashCap * 3), nr, a, ca - cs, ca);
-                p.nrec[c] = nr;
-            } else {
-                r.flag = 1;
-            }
+            if (met_at < b + kTile)   // the extraction fixes the records (row 0 and offsets)
+                r.flag = (uint8_t)((cur_flags & kFlagRow0Rec) | kFlagFixed | (ca > 0 ? kFlagPrefixHit : 0));
+            else
+                r.flag = kFlagRescan;
+            r.delta = ca - cs;
         }
     } else {
         r.count = ca;
         r.last = qa;
-        r.flag = 1;
+        r.flag = kFlagRescan;
     }
     return r;
 }
@@ -206,12 +190,13 @@ __device__ Repair repair_chunk(const ScanParams &p, const OneTable &T, uint64_t 
 __device__ __forceinline__ void apply_repair(const ScanParams &p, uint64_t c, uint32_t a,
                                              const Repair &r, uint32_t chunks_per_block,
                                              unsigned long long *sums) {
-    const uint32_t old = p.count[c];
+    const uint32_t old = r.old_count;
     p.count[c] = r.count;
     atomicAdd(&sums[c / chunks_per_block], (unsigned long long)(long long)((int64_t)r.count - (int64_t)old));
     p.spec_start[c] = a;
     p.last_state[c] = r.last;
-    if (r.flag) p.flags[c] = 1;
+    if (r.flag) p.flags[c] = r.flag;
+    if (r.flag & kFlagFixed) p.fix_delta[c] = r.delta;
 }
 
 // The join across blocks (Sec. III-A "binary reduction"), run by the last block to
@@ -287,7 +272,7 @@ __device__ void finalize_block(const ScanParams &p, const OneTable &T, unsigned 
                     if (k >= p.nseg || cur == p.spec_start[k]) { walked = k; break; }
                     const Repair r = repair_chunk(p, T, k, cur, p.spec_start[k], nullptr);
                     apply_repair(p, k, cur, r, cpb, sums);
-                    p.flags[k] = 1;   // its records follow a start that was not the true one
+                    p.flags[k] = kFlagRescan;   // its records follow a start that was not the true one
                     cur = r.last;
                     ++k;
                 }
@@ -439,6 +424,7 @@ scan_kernel(ScanParams p) {
     __syncthreads();
     uint32_t *stash = POS ? p.stash + seg * (kStashCap * 3) : nullptr;
     uint32_t nrec = 0;
+    bool row0rec = false;   // the chunk's row 0 has a hit-row record
 
     // ---- speculated start state: q0, or the state reached from q0 over the lookback window
     uint32_t q = 0;
@@ -513,9 +499,11 @@ scan_kernel(ScanParams p) {
                     err |= expect ^ w[k];
                 }
                 if ((err & 0xDFDFDFDFu) == 0) {
-                    if (POS && rc)
+                    if (POS && rc) {
+                        row0rec |= t == 0;
                         record_hit_row(stash, nrec, t | kRowAllBases,
                                        ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes, cnt);
+                    }
                     cnt += rc;
                     cur = c2 & 0x3FFFFu;
                     done = true;
@@ -528,7 +516,7 @@ scan_kernel(ScanParams p) {
                 // (the row was just staged, so it is in L2)
                 uint32_t qe = row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
                                                row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
-                if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
+                if (POS && cnt != before) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, before); }
                 cur = pair_base + qe * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
             }
         } else {
@@ -536,7 +524,7 @@ scan_kernel(ScanParams p) {
             q = full ? row_bytes_reg(T, qs, w, cnt)
                      : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
                                         row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
-            if (POS && cnt != before) record_hit_row(stash, nrec, t, qs, before);
+            if (POS && cnt != before) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, before); }
         }
     }
     cp_async_wait<0>();
@@ -552,6 +540,8 @@ scan_kernel(ScanParams p) {
     if (lane == 0) prev = warp > 0 ? warp_last[warp - 1] : 0u;
     const bool has_prev = active && seg > 0 && (lane > 0 || warp > 0);
     bool pending = false;   // a block's first chunk is joined by the last block directly
+    bool fixed = false, prefix_hit = false;
+    uint32_t fix_delta = 0;
     if (has_prev && prev != spec) {
         // run the true start and the speculated start in lockstep over the chunk's first
         // bytes; at the first step where their states are equal, the rest of the chunk is
@@ -575,7 +565,9 @@ scan_kernel(ScanParams p) {
         if (conv) {
             const uint32_t delta = pa - ps;   // modulo 2^32; the corrected count is exact
             cnt += delta;
-            if (POS) fix_hit_rows(stash, nrec, prev, delta, pa);
+            fix_delta = delta;
+            fixed = true;
+            prefix_hit = pa > 0;
             spec = prev;
         } else {
             pending = true;   // the last block repairs it from global memory
@@ -585,8 +577,16 @@ scan_kernel(ScanParams p) {
         p.spec_start[seg] = spec;
         p.last_state[seg] = last;
         p.count[seg] = cnt;
-        p.flags[seg] = 0;
-        if (POS) p.nrec[seg] = nrec;
+        if (POS) {
+            // the records stay those of the speculative run; the flags say how the
+            // extraction turns them into the true run's
+            p.flags[seg] = (row0rec ? kFlagRow0Rec : 0) |
+                           (fixed ? kFlagFixed | (prefix_hit ? kFlagPrefixHit : 0) : 0);
+            if (fixed) p.fix_delta[seg] = fix_delta;
+            p.nrec[seg] = nrec;
+        } else {
+            p.flags[seg] = 0;
+        }
     }
     if (pending) {
         const uint32_t k = atomicAdd(&p.ctrl[1], 1u);
