@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=10)
+    ap.add_argument("--batch-seqs", type=int, default=4096)
+    ap.add_argument("--batch-dfas", type=int, default=64)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-percall", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -206,7 +208,8 @@ def bench_batched(args, dna, torch, stream, clocks_mhz):
     """The batched configuration: one plan (autotuned, graph-captured), K timed runs;
     then the same pairs through one dna_scan call each."""
     import synth
-    buf, offs, regexes = synth.batched(n_states=lambda r: dna.compile_regex(r)[0].shape[0])
+    buf, offs, regexes = synth.batched(n_seqs=args.batch_seqs, n_dfas=args.batch_dfas,
+                                       n_states=lambda r: dna.compile_regex(r)[0].shape[0])
     n_s = offs.size - 1
     lens = [int(offs[i + 1] - offs[i]) for i in range(n_s)]
     total = int(offs[-1])
