@@ -164,49 +164,73 @@ inline size_t batch_smem_bytes(int warps, uint32_t max_states) {
     return (size_t)batch_one_off(warps) + (size_t)max_states * 16 + 2048 + (size_t)max_states * kPairRowBytes;
 }
 
-// 32 words = 512 bases through the pair table. Pair k of a word (bits 4k..4k+3) must
-// arrive at bits 7..10 of the mux operand with bits 27..30 clear: pairs 0..2 come from
-// the word's low 12 bits shifted left 7, 3 and right 1; pairs 3..7 from right shifts of
-// 5..21, which leave bits 27..30 zero.
-__device__ __forceinline__ uint32_t tile_pairs(uint32_t cur, const uint32_t (&w)[32], uint32_t k1,
-                                               uint32_t k5, uint32_t &cnt) {
-    uint32_t rc = 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const uint32_t wd = w[k];
-        const uint32_t lo = wd & 0xFFFu;
-        uint32_t e, acc;
-        e = lds_u32(mux_pair(cur, lo << 7)); acc = e;
-        e = lds_u32(mux_pair(e, lo << 3)); acc = mad_lo(e, k1, acc);
-        e = lds_u32(mux_pair(e, lo >> 1)); acc = mad_lo(e, k1, acc);
-        e = lds_u32(mux_pair(e, wd >> 5)); acc = mad_lo(e, k1, acc);
-        rc = mad_hi(acc, k5, rc);           // 4 entries: count <= 8 in bits 27..30
-        e = lds_u32(mux_pair(e, wd >> 9)); acc = e;
-        e = lds_u32(mux_pair(e, wd >> 13)); acc = mad_lo(e, k1, acc);
-        e = lds_u32(mux_pair(e, wd >> 17)); acc = mad_lo(e, k1, acc);
-        e = lds_u32(mux_pair(e, wd >> 21)); acc = mad_lo(e, k1, acc);
-        rc = mad_hi(acc, k5, rc);
-        cur = e;
-    }
-    cnt += rc;
-    return cur;
+// One word (16 bases) of a chain through the pair table. Pair k of the word (bits
+// 4k..4k+3) must arrive at bits 7..10 of the mux operand with bits 27..30 clear: pairs
+// 0..2 come from the word's low 12 bits shifted left 7, 3 and right 1; pairs 3..7 from
+// right shifts of 5..21, which leave bits 27..30 zero. Counts collect in bits 27..30 of
+// acc (4 entries, at most 8) and move into cnt twice per word.
+__device__ __forceinline__ uint32_t word_pairs(uint32_t cur, uint32_t wd, uint32_t k1, uint32_t k5, uint32_t &cnt) {
+    const uint32_t lo = wd & 0xFFFu;
+    uint32_t e, acc;
+    e = lds_u32(mux_pair(cur, lo << 7)); acc = e;
+    e = lds_u32(mux_pair(e, lo << 3)); acc = mad_lo(e, k1, acc);
+    e = lds_u32(mux_pair(e, lo >> 1)); acc = mad_lo(e, k1, acc);
+    e = lds_u32(mux_pair(e, wd >> 5)); acc = mad_lo(e, k1, acc);
+    cnt = mad_hi(acc, k5, cnt);
+    e = lds_u32(mux_pair(e, wd >> 9)); acc = e;
+    e = lds_u32(mux_pair(e, wd >> 13)); acc = mad_lo(e, k1, acc);
+    e = lds_u32(mux_pair(e, wd >> 17)); acc = mad_lo(e, k1, acc);
+    e = lds_u32(mux_pair(e, wd >> 21)); acc = mad_lo(e, k1, acc);
+    cnt = mad_hi(acc, k5, cnt);
+    return e;
 }
 
+// Walks bytes [from, to) of a sequence (offsets from the 16-byte aligned 'abase'; bytes at
+// or past 'hi' are never read past their 16-byte granule) with the one-symbol table from
+// state q, adding accepting steps to *cnt. Rare (steps with a reset byte or a sequence
+// end, lookback windows over them), so it is kept out of line with one load in flight.
+__device__ __noinline__ uint32_t walk_bytes(const OneTable &T, const uint8_t *abase, uint64_t from, uint64_t to,
+                                            uint64_t hi, uint32_t q, uint32_t *cnt) {
+    uint32_t c = 0;
+    for (uint64_t g = from & ~(uint64_t)15; g < to; g += 16) {
+        const uint4 v = g < hi ? *reinterpret_cast<const uint4 *>(abase + g) : make_uint4(0, 0, 0, 0);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const uint64_t o = g + (uint64_t)i;
+            if (o >= from && o < to) {
+                const uint32_t e = T.step(q, (w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+                q = e & 0x7FFFFFFFu;
+                c += e >> 31;
+            }
+        }
+    }
+    if (cnt) *cnt += c;
+    return q;
+}
+
+constexpr int kStepBases = 256;                // bases per lane per staging step (64 B)
+constexpr int kStepWords = 16;
+constexpr int kBatchRows = 64;                 // staged rows per warp: two chunks per lane
+
+// Persistent: each block takes tasks from the ticket. A lane walks two chunks (rows lane
+// and lane + 32 of its warp's 64) as two independent chains, so the lookups of one
+// chain overlap the latency of the other's.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) batch_kernel(BatchParams p) {
-    extern __shared__ __align__(2048) uint8_t smem[];
-    __shared__ unsigned long long row_src[WARPS][32];   // word offset of each row's chunk in 'codes'
-    __shared__ uint32_t row_tiles[WARPS][32];
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ unsigned long long row_src[WARPS][kBatchRows];   // word offset of each row's chunk in 'codes'
+    __shared__ uint32_t row_steps[WARPS][kBatchRows];
     __shared__ uint32_t task_s;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
-    const uint32_t stage_addr = smem_base + (uint32_t)warp * 32u * kTile;
-    const uint8_t *stage_ptr = smem + (size_t)warp * 32u * kTile;
+    const uint32_t stage_addr = smem_base + (uint32_t)warp * kBatchRows * 64u;
+    const uint8_t *stage_ptr = smem + (size_t)warp * kBatchRows * 64u;
     uint32_t *one_s = reinterpret_cast<uint32_t *>(smem + batch_one_off(WARPS));
     const uint32_t pair_base = (smem_base + batch_one_off(WARPS) + p.max_states * 16u + 2047u) & ~2047u;
     uint32_t *pair_s = reinterpret_cast<uint32_t *>(smem + (pair_base - smem_base));
-    const uint32_t l8 = (uint32_t)lane >> 3, cc = (uint32_t)lane & 7u;
+    const uint32_t r8 = (uint32_t)lane >> 2, cc = (uint32_t)lane & 3u;
     uint32_t cur_dfa = 0xFFFFFFFFu;
 
     for (;;) {
@@ -234,119 +258,135 @@ __global__ void __launch_bounds__(WARPS * 32, 1) batch_kernel(BatchParams p) {
         T.reset_entry = D.reset_entry;
         const uint64_t g_end = (tg + 1) * p.groups_per_task < p.n_groups ? (tg + 1) * p.groups_per_task : p.n_groups;
         for (uint64_t g = tg * p.groups_per_task; g < g_end; ++g) {
-            const uint64_t ci = (g * WARPS + warp) * 32u + lane;
-            const bool active = ci < p.n_chunks;
-            uint32_t s = 0xFFFFFFFFu, my_tiles = 0;
-            uint64_t base0 = 0, len = 0, ctile = 0;
-            if (active) {
-                const uint2 c = p.chunks[ci];
-                s = c.x;
-                len = p.lens[s];
-                base0 = (uint64_t)c.y * p.chunk_tiles * kBasesPerTile;
-                const uint64_t rem = len - base0;
-                const uint64_t cap = (uint64_t)p.chunk_tiles * kBasesPerTile;
-                my_tiles = (uint32_t)(((rem < cap ? rem : cap) + kBasesPerTile - 1) / kBasesPerTile);
-                ctile = p.tile0[s] + (uint64_t)c.y * p.chunk_tiles;
+            // the lane's two chunks: rows lane and lane + 32 of the warp's 64
+            uint32_t s[2] = {0xFFFFFFFFu, 0xFFFFFFFFu}, steps[2] = {0, 0}, cur[2], cnt[2] = {0, 0};
+            uint64_t base0[2] = {0, 0}, len[2] = {0, 0}, ctile[2] = {0, 0};
+            bool active[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t ci = (g * WARPS + warp) * kBatchRows + (uint64_t)(32 * h + lane);
+                active[h] = ci < p.n_chunks;
+                if (active[h]) {
+                    const uint2 c = p.chunks[ci];
+                    s[h] = c.x;
+                    len[h] = p.lens[c.x];
+                    base0[h] = (uint64_t)c.y * p.chunk_tiles * kBasesPerTile;
+                    const uint64_t rem = len[h] - base0[h];
+                    const uint64_t cap = (uint64_t)p.chunk_tiles * kBasesPerTile;
+                    steps[h] = (uint32_t)(((rem < cap ? rem : cap) + kStepBases - 1) / kStepBases);
+                    ctile[h] = p.tile0[c.x] + (uint64_t)c.y * p.chunk_tiles;
+                }
+                row_src[warp][32 * h + lane] = ctile[h] * kWordsPerTile;
+                row_steps[warp][32 * h + lane] = steps[h];
             }
-            row_src[warp][lane] = ctile * kWordsPerTile;
-            row_tiles[warp][lane] = my_tiles;
             __syncwarp();
-            const uint32_t ntiles = __reduce_max_sync(0xFFFFFFFFu, my_tiles);
-            // copy j of a lane moves 16-byte column cc of row 4j + l8 (rows past their
-            // chunk's end are zero-filled and never read)
-            auto issue = [&](uint32_t t) {
+            const uint32_t nsteps = __reduce_max_sync(0xFFFFFFFFu, steps[0] > steps[1] ? steps[0] : steps[1]);
+            // copy j of a lane moves 16-byte column cc of row 8j + lane/4 (rows past their
+            // chunk's end are zero-filled and never read); column c of row r sits at slot
+            // c ^ ((r >> 1) & 3), so the lanes of each 128-bit read phase hit distinct banks
+            auto issue = [&](uint32_t st) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const uint32_t r = 4u * j + l8;
-                    const bool ok = t < row_tiles[warp][r];
-                    const uint32_t *src = p.codes + row_src[warp][r] + (uint64_t)t * kWordsPerTile + cc * 4u;
-                    const uint32_t dst = stage_addr + r * kTile + ((cc ^ (r & 7u)) << 4);
+                    const uint32_t r = 8u * j + r8;
+                    const bool ok = st < row_steps[warp][r];
+                    const uint32_t *src = p.codes + row_src[warp][r] + (uint64_t)st * kStepWords + cc * 4u;
+                    const uint32_t dst = stage_addr + r * 64u + ((cc ^ ((r >> 1) & 3u)) << 4);
                     cp_async16(dst, ok ? (const void *)src : (const void *)p.codes, ok ? 16u : 0u);
                 }
             };
-            if (ntiles) issue(0);
+            if (nsteps) issue(0);
             cp_async_commit();
 
-            // exact start state: run from q0 over the 'lookback' bases in front of the chunk
-            // (they lie in the previous tile of the same sequence)
-            uint32_t cur = pair_base + (uint32_t)lane * 4u;   // state 0, this lane's copy
-            uint32_t cnt = 0;
-            if (active && base0 > 0 && D.lookback > 0) {
-                const uint64_t pt = ctile - 1;
-                if (p.tflags[pt] == 0) {
-                    const uint32_t nw = D.lookback / 16u;
-                    const uint32_t *lw = p.codes + pt * kWordsPerTile + (kWordsPerTile - nw);
-                    for (uint32_t i = 0; i < nw; ++i) {
-                        const uint32_t wd = lw[i];
+            // exact start states: run from q0 over the 'lookback' bases in front of each
+            // chunk (they lie in the previous tile of the same sequence)
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const uint32_t op = q == 0 ? (wd & 0xFFFu) << 7 : q == 1 ? (wd & 0xFFFu) << 3
-                                              : q == 2 ? (wd & 0xFFFu) >> 1 : wd >> (4 * q - 7);
-                            cur = lds_u32(mux_pair(cur, op));
-                        }
+            for (int h = 0; h < 2; ++h) {
+                cur[h] = pair_base + (uint32_t)lane * 4u;   // state 0, this lane's copy
+                if (active[h] && base0[h] > 0 && D.lookback > 0) {
+                    const uint64_t pt = ctile[h] - 1;
+                    if (p.tflags[pt] == 0) {
+                        const uint32_t nw = D.lookback / 16u;
+                        const uint32_t *lw = p.codes + pt * kWordsPerTile + (kWordsPerTile - nw);
+                        uint32_t discard = 0;
+                        for (uint32_t i = 0; i < nw; ++i) cur[h] = word_pairs(cur[h], lw[i], p.k1, p.k5, discard);
+                    } else {
+                        const uint8_t *src = p.seqs[s[h]];
+                        const uint64_t sh = (uint64_t)((uintptr_t)src & 15u);
+                        const uint32_t q = walk_bytes(T, src - sh, sh + base0[h] - D.lookback, sh + base0[h],
+                                                      sh + len[h], 0u, nullptr);
+                        cur[h] = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
                     }
-                } else {
-                    const uint8_t *src = p.seqs[s];
-                    const uint64_t sh = (uint64_t)((uintptr_t)src & 15u);
-                    uint32_t q = 0;
-                    walk_range(src - sh, sh + base0 - D.lookback, sh + base0, sh + len,
-                               [&](uint64_t, uint32_t byte) { q = T.step(q, byte) & 0x7FFFFFFFu; return true; });
-                    cur = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
                 }
             }
-            uint8_t flag_next = active && my_tiles ? p.tflags[ctile] : 0;
-            for (uint32_t t = 0; t < ntiles; ++t) {
+            for (uint32_t st = 0; st < nsteps; ++st) {
                 cp_async_wait<0>();
                 __syncwarp();
-                uint32_t w[32];
-                {
-                    const uint8_t *srow = stage_ptr + lane * kTile;
+                uint32_t wa[kStepWords], wb[kStepWords];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((c ^ (lane & 7)) * 16));
-                        w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
-                    }
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t ra = (uint32_t)lane, rb = (uint32_t)lane + 32u;
+                    const uint4 va = *reinterpret_cast<const uint4 *>(stage_ptr + ra * 64u + ((c ^ ((ra >> 1) & 3u)) << 4));
+                    const uint4 vb = *reinterpret_cast<const uint4 *>(stage_ptr + rb * 64u + ((c ^ ((rb >> 1) & 3u)) << 4));
+                    wa[4 * c] = va.x; wa[4 * c + 1] = va.y; wa[4 * c + 2] = va.z; wa[4 * c + 3] = va.w;
+                    wb[4 * c] = vb.x; wb[4 * c + 1] = vb.y; wb[4 * c + 2] = vb.z; wb[4 * c + 3] = vb.w;
                 }
                 __syncwarp();
-                if (t + 1 < ntiles) issue(t + 1);
+                if (st + 1 < nsteps) issue(st + 1);
                 cp_async_commit();
-                const uint8_t flag = flag_next;
-                if (t + 1 < my_tiles) flag_next = p.tflags[ctile + t + 1];
-                if (t >= my_tiles) continue;
-                if (flag == 0) {
-                    cur = tile_pairs(cur, w, p.k1, p.k5, cnt);
+                // a step is 256 bases, half of an ingest tile; flagged tiles are walked byte by byte
+                const bool live_a = st < steps[0], live_b = st < steps[1];
+                const bool fast_a = live_a && p.tflags[ctile[0] + (st >> 1)] == 0;
+                const bool fast_b = live_b && p.tflags[ctile[1] + (st >> 1)] == 0;
+                if (fast_a && fast_b) {
+#pragma unroll
+                    for (int kk = 0; kk < kStepWords; ++kk) {
+                        cur[0] = word_pairs(cur[0], wa[kk], p.k1, p.k5, cnt[0]);
+                        cur[1] = word_pairs(cur[1], wb[kk], p.k1, p.k5, cnt[1]);
+                    }
                 } else {
-                    // a reset byte or the sequence end in this tile: walk its bytes
-                    uint32_t q = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-                    const uint8_t *src = p.seqs[s];
-                    const uint64_t sh = (uint64_t)((uintptr_t)src & 15u);
-                    const uint64_t tb = base0 + (uint64_t)t * kBasesPerTile;
-                    const uint64_t te = tb + kBasesPerTile < len ? tb + kBasesPerTile : len;
-                    walk_range(src - sh, sh + tb, sh + te, sh + len, [&](uint64_t, uint32_t byte) {
-                        const uint32_t e = T.step(q, byte);
-                        q = e & 0x7FFFFFFFu;
-                        cnt += e >> 31;
-                        return true;
-                    });
-                    cur = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const bool live = h ? live_b : live_a;
+                        const bool fast = h ? fast_b : fast_a;
+                        if (!live) continue;
+                        if (fast) {
+#pragma unroll
+                            for (int kk = 0; kk < kStepWords; ++kk)
+                                cur[h] = word_pairs(cur[h], h ? wb[kk] : wa[kk], p.k1, p.k5, cnt[h]);
+                        } else {
+                            // a reset byte or the sequence end in this step's 256 bases
+                            const uint32_t q0 = ((cur[h] & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+                            const uint8_t *src = p.seqs[s[h]];
+                            const uint64_t sh = (uint64_t)((uintptr_t)src & 15u);
+                            const uint64_t tb = base0[h] + (uint64_t)st * kStepBases;
+                            const uint64_t te = tb + kStepBases < len[h] ? tb + kStepBases : len[h];
+                            uint32_t c2 = cnt[h];
+                            const uint32_t q = walk_bytes(T, src - sh, sh + tb, sh + te, sh + len[h], q0, &c2);
+                            cnt[h] = c2;
+                            cur[h] = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
+                        }
+                    }
                 }
             }
             cp_async_wait<0>();
             // add the lane counts per sequence (a warp's chunks are ordered by sequence,
             // so usually one or two distinct sequences)
-            unsigned todo = __ballot_sync(0xFFFFFFFFu, active);
-            while (todo) {
-                const int leader = __ffs(todo) - 1;
-                const uint32_t key = __shfl_sync(0xFFFFFFFFu, s, leader);
-                const bool mine = active && s == key;
-                uint32_t v = mine ? cnt : 0u;
 #pragma unroll
-                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                if (lane == leader && v)
-                    atomicAdd(p.out + (uint64_t)key * p.out_stride + D.col, (unsigned long long)v);
-                todo &= ~__ballot_sync(0xFFFFFFFFu, mine);
+            for (int h = 0; h < 2; ++h) {
+                unsigned todo = __ballot_sync(0xFFFFFFFFu, active[h]);
+                while (todo) {
+                    const int leader = __ffs(todo) - 1;
+                    const uint32_t key = __shfl_sync(0xFFFFFFFFu, s[h], leader);
+                    const bool mine = active[h] && s[h] == key;
+                    uint32_t v = mine ? cnt[h] : 0u;
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                    if (lane == leader && v)
+                        atomicAdd(p.out + (uint64_t)key * p.out_stride + D.col, (unsigned long long)v);
+                    todo &= ~__ballot_sync(0xFFFFFFFFu, mine);
+                }
             }
-            __syncwarp();   // row_src / row_tiles are rewritten by the next group
+            __syncwarp();   // row_src / row_steps are rewritten by the next group
         }
     }
 }
@@ -361,7 +401,7 @@ BatchFn batch_fn(int warps) {
     }
 }
 
-// static shared memory of batch_kernel<W> (row_src, row_tiles, task_s), as compiled
+// static shared memory of batch_kernel<W> (row_src, row_steps, task_s), as compiled
 size_t batch_static_smem(int warps) {
     static std::atomic<size_t> cached[3] = {};
     const int i = warps == 8 ? 0 : warps == 16 ? 1 : 2;
@@ -369,7 +409,7 @@ size_t batch_static_smem(int warps) {
     if (v == 0) {
         cudaFuncAttributes a;
         v = cudaFuncGetAttributes(&a, (const void *)batch_fn(warps)) == cudaSuccess && a.sharedSizeBytes
-                ? a.sharedSizeBytes : (size_t)warps * 32 * 12 + 1024;
+                ? a.sharedSizeBytes : (size_t)warps * kBatchRows * 12 + 1024;
         cached[i].store(v, std::memory_order_relaxed);
     }
     return v;
@@ -450,7 +490,7 @@ int batch_plan_kernel(dna_batch &b, uint32_t chunk_tiles, uint32_t warps, cudaSt
     int per_sm = 0;
     DNA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)warps * 32, dyn));
     if (per_sm < 1) return DNA_ERR_CAPACITY;
-    const uint64_t lanes = (uint64_t)warps * 32;
+    const uint64_t lanes = (uint64_t)warps * kBatchRows;   // chunks per group
     const uint64_t n_groups = (b.n_chunks + lanes - 1) / lanes;
     const int slots = device_props(b.device).sms * per_sm;
     // a task is several chunk groups with one automaton (one table load); aim for at
@@ -465,7 +505,7 @@ int batch_plan_kernel(dna_batch &b, uint32_t chunk_tiles, uint32_t warps, cudaSt
 }
 
 void fill_params(const dna_batch &b, BatchParams &bp, unsigned long long *out) {
-    const uint64_t lanes = (uint64_t)b.warps * 32;
+    const uint64_t lanes = (uint64_t)b.warps * kBatchRows;   // chunks per group
     bp.codes = b.d_codes; bp.tflags = b.d_tflags; bp.seqs = b.d_seqs; bp.lens = b.d_lens;
     bp.tile0 = b.d_tile0; bp.chunks = b.d_chunks; bp.n_chunks = b.n_chunks;
     bp.chunk_tiles = b.chunk_tiles; bp.groups_per_task = b.groups_per_task;
