@@ -167,22 +167,25 @@ inline size_t batch_smem_bytes(int warps, uint32_t max_states) {
 // One word (16 bases) of a chain through the pair table. Pair k of the word (bits
 // 4k..4k+3) must arrive at bits 7..10 of the mux operand with bits 27..30 clear: pairs
 // 0..2 come from the word's low 12 bits shifted left 7, 3 and right 1; pairs 3..7 from
-// right shifts of 5..21, which leave bits 27..30 zero. Counts collect in bits 27..30 of
-// acc (4 entries, at most 8) and move into cnt twice per word.
+// right shifts of 5..21, which leave bits 27..30 zero. The 8 entries are summed as they
+// arrive: their address parts add up to less than 2^21 and bits 29..31 are zero, so the
+// pair counts (at most 16) land in bits 27..31 of the sum, which moves into cnt once.
 __device__ __forceinline__ uint32_t word_pairs(uint32_t cur, uint32_t wd, uint32_t k1, uint32_t k5, uint32_t &cnt) {
+    (void)k1;
     const uint32_t lo = wd & 0xFFFu;
-    uint32_t e, acc;
-    e = lds_u32(mux_pair(cur, lo << 7)); acc = e;
-    e = lds_u32(mux_pair(e, lo << 3)); acc = mad_lo(e, k1, acc);
-    e = lds_u32(mux_pair(e, lo >> 1)); acc = mad_lo(e, k1, acc);
-    e = lds_u32(mux_pair(e, wd >> 5)); acc = mad_lo(e, k1, acc);
-    cnt = mad_hi(acc, k5, cnt);
-    e = lds_u32(mux_pair(e, wd >> 9)); acc = e;
-    e = lds_u32(mux_pair(e, wd >> 13)); acc = mad_lo(e, k1, acc);
-    e = lds_u32(mux_pair(e, wd >> 17)); acc = mad_lo(e, k1, acc);
-    e = lds_u32(mux_pair(e, wd >> 21)); acc = mad_lo(e, k1, acc);
-    cnt = mad_hi(acc, k5, cnt);
-    return e;
+    const uint32_t e0 = lds_u32(mux_pair(cur, lo << 7));
+    const uint32_t e1 = lds_u32(mux_pair(e0, lo << 3));
+    const uint32_t e2 = lds_u32(mux_pair(e1, lo >> 1));
+    uint32_t t = e0 + e1 + e2;
+    const uint32_t e3 = lds_u32(mux_pair(e2, wd >> 5));
+    const uint32_t e4 = lds_u32(mux_pair(e3, wd >> 9));
+    t = t + e3 + e4;
+    const uint32_t e5 = lds_u32(mux_pair(e4, wd >> 13));
+    const uint32_t e6 = lds_u32(mux_pair(e5, wd >> 17));
+    t = t + e5 + e6;
+    const uint32_t e7 = lds_u32(mux_pair(e6, wd >> 21));
+    cnt = mad_hi(t + e7, k5, cnt);      // cnt += sum >> 27
+    return e7;
 }
 
 // Walks bytes [from, to) of a sequence (offsets from the 16-byte aligned 'abase'; bytes at
