@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-percall", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-plain-configs", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4000)
     return ap.parse_args()
 
@@ -399,6 +400,66 @@ def bench_serve(args, dna, torch):
 
 
 
+def bench_plain_configs(dna, torch, stream, peak):
+    """The other plain workloads: 1 MiB i.i.d. with TATAAA (count + positions; launch-bound
+    at this size) and 3.2 GiB with soft-masked and N runs against the Aho-Corasick
+    automaton of 1,000 random 12-mers (count only)."""
+    import synth
+    out = {}
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def kernel_ms(fn, steps):
+        dna.profile_read(reset=True)
+        dna.profile_enable(True)
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        dna.profile_enable(False)
+        pr = dna.profile_read(reset=True)
+        return pr["scan_kernel_ms"] / max(1, pr["scan_kernel_calls"])
+
+    seq, motif = synth.plain_small()
+    dfa = dna.Dfa.from_regex(motif)
+    d = torch.from_numpy(seq).cuda()
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    pos = torch.empty(1 << 12, dtype=torch.int64, device="cuda")
+    fn = lambda: dna.scan(dfa, d, positions=True, stream=stream, out_count=cnt, out_positions=pos)
+    ms = timed(fn, 2000)
+    out["small_1MiB_TATAAA"] = {"bytes": int(seq.size), "ms_per_step": ms, "gbs": seq.size / (ms * 1e-3) / 1e9,
+                                "matches": int(cnt.item()), "output": "count + positions",
+                                "note": "launch-bound: two kernels of about 10 us each"}
+    del d
+    seq, kmers = synth.plain_large()
+    dfa = dna.Dfa.from_kmers(kmers)
+    info = dfa.info()
+    d = torch.from_numpy(seq).cuda()
+    n = seq.size
+    del seq
+    fn = lambda: dna.scan(dfa, d, stream=stream, out_count=cnt)
+    ms = timed(fn, 10)
+    kms = kernel_ms(fn, 5)
+    out["large_3_2GiB_AC1000"] = {
+        "bytes": n, "ms_per_step": ms, "gbs": n / (ms * 1e-3) / 1e9, "matches": int(cnt.item()),
+        "n_states": info.n_states, "placement": ["auto", "smem pair", "smem one-symbol", "global one-symbol"][info.placement],
+        "kernel_ms": kms, "hbm_frac": n / (kms * 1e-3) / 1e9 / peak, "output": "count"}
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -508,6 +569,10 @@ def main():
                "sample": f"{done / MiB:.0f} MiB scanned as 32 MiB slices of the 256 MiB workload "
                          f"(count + positions), single thread"}
 
+    plain_configs = None
+    if world == 1 and not args.no_plain_configs:
+        plain_configs = bench_plain_configs(dna, torch, stream, load_peaks()[0])
+
     batched = None
     if world == 1 and not args.no_batched:
         batched = bench_batched(args, dna, torch, stream, clocks.get("sm_mhz"))
@@ -535,6 +600,7 @@ def main():
                     "d2h_bytes_per_step": 8 + 8 * n_matches, "ms_per_step": e2e_ms,
                     "api": "dna_scan_host (pinned host buffers, synchronous)"},
             "gpu_launches": launches,
+            "plain_configs": plain_configs,
             "batched": batched,
             "serve": serve,
             "clocks": clocks,
