@@ -87,12 +87,19 @@ typedef struct {
     uint32_t placement;        /* DNA_PLACE_* chosen for this automaton */
     uint32_t accept_start;     /* 1 when state 0 is in F */
     int32_t  device;
+    uint32_t chunk_maps;       /* 1 when scans run every chunk from every state (see DNA_PLACE_MAP) */
 } dna_dfa_info;
 
 #define DNA_PLACE_AUTO       0
 #define DNA_PLACE_SMEM_PAIR  1  /* two-symbol table, one copy per lane, shared memory */
 #define DNA_PLACE_SMEM_ONE   2  /* one-symbol table in shared memory */
 #define DNA_PLACE_GLOBAL_ONE 3  /* one-symbol table in global memory (L2 resident) */
+/* Chunk maps (automata of at most 32 states): a warp runs each chunk from every state at
+ * once (the possible starting states of Sec. III-A taken in full), a join composes the
+ * chunk maps in order. dfa_load picks it for automata whose runs from different states
+ * do not meet within 16 symbols of random DNA (speculation would rarely be repaired in
+ * the chunk's first bytes); it can also be requested through dna_plan.placement. */
+#define DNA_PLACE_MAP        4
 
 int dfa_info(const dna_dfa *dfa, dna_dfa_info *out);
 
@@ -171,7 +178,7 @@ int dna_scan_count_static(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
  *   lookback       symbols read before a chunk to speculate its start state
  *                  (1 = the paper's possible starting states from one symbol);
  *                  0 = automatic; at most 64.
- *   warps_per_cta  4, 8 or 16; 0 = automatic.
+ *   warps_per_cta  8, 16, 24 or 32; 0 = automatic.
  *   placement      DNA_PLACE_*; 0 = automatic. A placement the automaton does not fit
  *                  in returns DNA_ERR_CAPACITY.
  *   prefetch_tiles how many 128-byte tiles ahead each lane prefetches its chunk into L2;

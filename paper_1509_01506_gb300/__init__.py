@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 DNA_OK = 0
-PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE = 0, 1, 2, 3
+PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE, PLACE_MAP = 0, 1, 2, 3, 4
 
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
@@ -42,7 +42,8 @@ class DnaError(RuntimeError):
 class _Info(ctypes.Structure):
     _fields_ = [("n_states", ctypes.c_uint32), ("definite_depth", ctypes.c_int32),
                 ("lookback", ctypes.c_uint32), ("placement", ctypes.c_uint32),
-                ("accept_start", ctypes.c_uint32), ("device", ctypes.c_int32)]
+                ("accept_start", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("chunk_maps", ctypes.c_uint32)]
 
 
 class _Plan(ctypes.Structure):
@@ -232,6 +233,7 @@ class DfaInfo:
     placement: int
     accept_start: bool
     device: int
+    chunk_maps: bool
 
 
 class Dfa:
@@ -269,7 +271,7 @@ class Dfa:
         i = _Info()
         _check(lib().dfa_info(self.handle, ctypes.byref(i)), "dfa_info")
         return DfaInfo(i.n_states, i.definite_depth, i.lookback, i.placement,
-                       bool(i.accept_start), i.device)
+                       bool(i.accept_start), i.device, bool(i.chunk_maps))
 
     def free(self):
         if self._h:

@@ -1,0 +1,298 @@
+// dna_map.cu -- the chunk-map path for automata whose runs do not converge.
+//
+// Speculation with repair (dna_scan.cu) relies on the runs from different start states
+// meeting soon (the converging point of Sec. III-B.3). Some automata never synchronise
+// on DNA (permutation-like tables, counters): there every chunk's repair walks the whole
+// chunk and every join cascades, serially. For those the scan follows the paper's
+// possible-starting-state approach in full (Sec. III-A): a chunk is run from every state
+// at once. With at most 32 states a warp owns a chunk and lane q carries start state q;
+// all lanes read the same bytes. Each chunk yields a map (end state and count per start
+// state) and the state at each of its 32 sub-chunk boundaries per start. A single-block
+// join composes the maps in order (chunk c starts in the end state of chunk c-1 from its
+// true start), which gives the total count and every sub-chunk's exact start state. The
+// positions come from the single-sequence kernels run with those exact starts.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/dna_dfa.h"
+#include "dna_device.cuh"
+#include "dna_runtime.h"
+
+using namespace dnalib;
+
+namespace {
+
+constexpr int kMapWarps = 24;
+constexpr int kMapTile = 512;          // bytes staged per warp per step (4 rows of 128)
+constexpr uint32_t kMapSubs = 32;      // sub-chunks per chunk (one per lane in the positions pass)
+constexpr int kJoinWarps = 16;
+
+struct MapParams {
+    const uint8_t *abase;       // 16-byte aligned base; sequence byte j is abase[lo + j]
+    uint64_t lo, hi;
+    uint64_t chunk_bytes;       // multiple of kMapSubs * kTile
+    uint32_t n_chunks;
+    uint32_t n_states;          // <= 32
+    uint32_t reset_entry;
+    const uint32_t *one;        // [n_states][4] next | accept << 31, code order A, C, T, G
+    const uint32_t *pair;       // [n_states][16] compact pair entries next | count << 24
+    uint32_t *map_end;          // [n_chunks][32] end state per start state
+    uint32_t *map_cnt;          // [n_chunks][32] accepting steps per start state
+    uint32_t *bound;            // [n_chunks][32 sub-chunks][32 start states]
+    uint32_t k1, k5, lut_lo, lut_hi;
+};
+
+// One warp per chunk; lane q runs the chunk from state q (lanes at or past n_states run
+// from state 0 and are ignored). The chunk's bytes are staged 512 at a time and read by
+// every lane from the same shared address.
+__global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
+    // shared memory: [stages: warps x 2 x 512 B][one-symbol table: 32 x 16 B][pad][pair table]
+    uint8_t *stage = smem + (size_t)warp * 2 * kMapTile;
+    const uint32_t stage_addr = smem_base + (uint32_t)warp * 2 * kMapTile;
+    uint32_t *one_s = reinterpret_cast<uint32_t *>(smem + (size_t)kMapWarps * 2 * kMapTile);
+    const uint32_t pair_base = (smem_base + kMapWarps * 2 * kMapTile + 32 * 16 + 2047u) & ~2047u;
+    uint32_t *pair_s = reinterpret_cast<uint32_t *>(smem + (pair_base - smem_base));
+    for (uint32_t i = threadIdx.x; i < p.n_states * 4u; i += kMapWarps * 32) one_s[i] = p.one[i];
+    for (uint32_t i = threadIdx.x; i < p.n_states * 16u * 32u; i += kMapWarps * 32) {
+        const uint32_t e = p.pair[i >> 5];
+        pair_s[i] = ((e >> 24) << kCountShift) |
+                    (pair_base + (e & 0x00FFFFFFu) * (uint32_t)kPairRowBytes + (i & 31u) * 4u);
+    }
+    __syncthreads();
+    const uint32_t c = blockIdx.x * kMapWarps + warp;
+    if (c >= p.n_chunks) return;   // warp-uniform; no barrier follows
+
+    OneTable T;
+    T.t = one_s;
+    T.reset_entry = p.reset_entry;
+    const uint64_t b = (uint64_t)c * p.chunk_bytes;
+    const uint64_t from = b > p.lo ? b : p.lo;
+    const uint64_t to = b + p.chunk_bytes < p.hi ? b + p.chunk_bytes : p.hi;
+    const uint64_t sub = p.chunk_bytes / kMapSubs;
+    const uint32_t ntiles = (uint32_t)((to - b + kMapTile - 1) / kMapTile);
+    const uint32_t q0 = (uint32_t)lane < p.n_states ? (uint32_t)lane : 0u;
+    uint32_t cur = pair_base + q0 * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
+    uint32_t cnt = 0;
+    auto issue = [&](uint32_t t) {   // lane copies 16 bytes of tile t (granules past hi zero-filled)
+        const uint64_t g = b + (uint64_t)t * kMapTile + (uint64_t)lane * 16u;
+        const bool ok = g < p.hi;
+        cp_async16(stage_addr + (t & 1u) * kMapTile + (uint32_t)lane * 16u, ok ? p.abase + g : p.abase, ok ? 16u : 0u);
+    };
+    issue(0);
+    cp_async_commit();
+    for (uint32_t t = 0; t < ntiles; ++t) {
+        if (t + 1 < ntiles) issue(t + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const uint8_t *tile = stage + (t & 1u) * kMapTile;
+#pragma unroll 1
+        for (int r = 0; r < kMapTile / kTile; ++r) {
+            const uint64_t ro = b + (uint64_t)t * kMapTile + (uint64_t)r * kTile;
+            if (ro >= to) break;
+            if ((ro - b) % sub == 0)   // a sub-chunk starts here: record every lane's state
+                p.bound[((uint64_t)c * kMapSubs + (ro - b) / sub) * 32u + lane] =
+                    ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+            const uint8_t *row = tile + r * kTile;
+            const bool full = ro >= from && ro + kTile <= to;
+            bool done = false;
+            if (full) {
+                uint32_t w[32];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(row + 16 * i);
+                    w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+                }
+                uint32_t acc = 0, err = 0, rc = 0, c2 = cur;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const uint32_t x = w[k] & 0x06060606u;
+                    const uint32_t y = mad_lo(x, 65u, 0u);
+                    const uint32_t e1 = lds_u32(mux_pair(c2, y));
+                    const uint32_t e2 = lds_u32(mux_pair(e1, y >> 16));
+                    acc = mad_lo(e1, p.k1, acc);
+                    acc = mad_lo(e2, p.k1, acc);
+                    c2 = e2;
+                    if (k % 3 == 2 || k == 31) {
+                        rc = mad_hi(acc, p.k5, rc);
+                        acc = 0;
+                    }
+                    const uint32_t z = x | (x >> 4);
+                    err |= __byte_perm(p.lut_lo, p.lut_hi, __byte_perm(z, 0, 0x0020)) ^ w[k];
+                }
+                if ((err & 0xDFDFDFDFu) == 0) {
+                    cnt += rc;
+                    cur = c2 & 0x3FFFFu;
+                    done = true;
+                }
+            }
+            if (!done) {
+                // reset bytes or a sequence edge in this row: byte by byte
+                uint32_t q = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+                const uint32_t k0 = ro < from ? (uint32_t)(from - ro) : 0u;
+                const uint32_t k1 = ro + kTile > to ? (uint32_t)(to - ro) : (uint32_t)kTile;
+                for (uint32_t k = k0; k < k1; ++k) {
+                    const uint32_t e = T.step(q, row[k]);
+                    q = e & 0x7FFFFFFFu;
+                    cnt += e >> 31;
+                }
+                cur = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
+            }
+        }
+        __syncwarp();   // every lane is done with this stage before it is refilled
+    }
+    cp_async_wait<0>();
+    p.map_end[(uint64_t)c * 32u + lane] = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+    p.map_cnt[(uint64_t)c * 32u + lane] = cnt;
+}
+
+struct JoinParams {
+    const uint32_t *map_end, *map_cnt, *bound;
+    uint32_t n_chunks;
+    uint32_t *given;            // [n_chunks * 32] exact start of each sub-chunk, or null
+    uint64_t *out_count;
+};
+
+// Single block. Chunks are taken 32 at a time: a warp composes a group's 32 maps for all
+// start states (lane q follows start q), thread 0 then chains the groups from state 0,
+// and (for the positions pass) each group is walked again from its true start to give
+// every chunk's, and so every sub-chunk's, exact start.
+__global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams p) {
+    extern __shared__ __align__(16) uint32_t jsm[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t ng = (p.n_chunks + 31) / 32;
+    uint32_t *g_end = jsm;                      // [ng][32]
+    uint32_t *g_cnt = g_end + ng * 32;          // [ng][32]
+    uint32_t *g_start = g_cnt + ng * 32;        // [ng]
+    uint32_t *wbuf = g_start + ng;              // per warp: [32 chunks][32] ends, then counts
+    uint32_t *my_end = wbuf + (size_t)warp * 2048;
+    uint32_t *my_cnt = my_end + 1024;
+    auto load_group = [&](uint32_t g) {
+        const uint32_t nk = p.n_chunks - g * 32 < 32 ? p.n_chunks - g * 32 : 32;
+        for (uint32_t i = lane; i < nk * 32; i += 32) {
+            my_end[i] = p.map_end[(uint64_t)g * 1024 + i];
+            my_cnt[i] = p.map_cnt[(uint64_t)g * 1024 + i];
+        }
+        __syncwarp();
+        return nk;
+    };
+    for (uint32_t g = warp; g < ng; g += kJoinWarps) {
+        const uint32_t nk = load_group(g);
+        uint32_t s = (uint32_t)lane, cc = 0;
+        for (uint32_t k = 0; k < nk; ++k) {
+            cc += my_cnt[k * 32 + s];
+            s = my_end[k * 32 + s];
+        }
+        g_end[g * 32 + lane] = s;
+        g_cnt[g * 32 + lane] = cc;
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        unsigned long long total = 0;
+        for (uint32_t g = 0; g < ng; ++g) {
+            g_start[g] = s;
+            total += g_cnt[g * 32 + s];
+            s = g_end[g * 32 + s];
+        }
+        *p.out_count = total;
+    }
+    __syncthreads();
+    if (!p.given) return;
+    for (uint32_t g = warp; g < ng; g += kJoinWarps) {
+        const uint32_t nk = load_group(g);
+        uint32_t s = g_start[g];
+        for (uint32_t k = 0; k < nk; ++k) {
+            const uint64_t c = (uint64_t)g * 32 + k;
+            p.given[c * kMapSubs + lane] = p.bound[(c * kMapSubs + lane) * 32u + s];
+            s = my_end[k * 32 + s];
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+namespace dnalib {
+
+// The chunk-map scan of one sequence (count, and positions through scan_impl with the
+// exact sub-chunk starts). Requires n_states <= 32.
+int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream, uint64_t *out_count,
+                  uint64_t *out_positions, uint64_t cap) {
+    if (d->n_states > 32 || !d->d_pair) return DNA_ERR_INVALID_ARG;
+    const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
+    const uint8_t *abase = seq - shift;
+    const uint64_t total = len + shift;
+    const DeviceProps pr = device_props(d->device);
+    const uint64_t warps = (uint64_t)(pr.sms ? pr.sms : 152) * kMapWarps;   // one wave of chunk warps
+    const uint64_t unit = (uint64_t)kMapSubs * kTile;                        // 4 KiB
+    uint64_t S = (total + warps - 1) / warps;
+    S = (S + unit - 1) / unit * unit;
+    const uint32_t n_chunks = (uint32_t)((total + S - 1) / S);
+    const bool positions = out_positions != nullptr && cap > 0;
+    const size_t n32 = (size_t)n_chunks * 32;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_end = take(n32 * 4), o_cnt = take(n32 * 4), o_bound = take(n32 * kMapSubs * 4);
+    const size_t o_given = positions ? take(n32 * 4) : 0;
+    void *mem = nullptr;
+    DNA_CUDA(cudaMallocAsync(&mem, off, stream));
+    uint8_t *base = (uint8_t *)mem;
+
+    MapParams mp;
+    mp.abase = abase; mp.lo = shift; mp.hi = total; mp.chunk_bytes = S; mp.n_chunks = n_chunks;
+    mp.n_states = d->n_states; mp.reset_entry = d->reset_entry; mp.one = d->d_one; mp.pair = d->d_pair;
+    mp.map_end = (uint32_t *)(base + o_end); mp.map_cnt = (uint32_t *)(base + o_cnt);
+    mp.bound = (uint32_t *)(base + o_bound);
+    mp.k1 = 1u; mp.k5 = 32u; mp.lut_lo = 0x00630061u; mp.lut_hi = 0x00670074u;
+    const size_t msmem = (size_t)kMapWarps * 2 * kMapTile + 32 * 16 + 2048 + (size_t)d->n_states * kPairRowBytes;
+    const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
+    int rc = ensure_smem_optin((const void *)map_kernel, d->device, optin - 1024);
+    cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
+    if (e == cudaSuccess) {
+        const ProfToken tk = prof_begin(stream);
+        map_kernel<<<(n_chunks + kMapWarps - 1) / kMapWarps, kMapWarps * 32, msmem, stream>>>(mp);
+        e = cudaGetLastError();
+        prof_end(tk, stream, PROF_SCAN);
+        record_launch();
+    }
+    JoinParams jp;
+    jp.map_end = mp.map_end; jp.map_cnt = mp.map_cnt; jp.bound = mp.bound; jp.n_chunks = n_chunks;
+    jp.given = positions ? (uint32_t *)(base + o_given) : nullptr;
+    jp.out_count = out_count;
+    const uint32_t ng = (n_chunks + 31) / 32;
+    const size_t jsmem = ((size_t)ng * 65 + (size_t)kJoinWarps * 2048) * 4;
+    if (e == cudaSuccess) {
+        rc = ensure_smem_optin((const void *)map_join_kernel, d->device, optin - 1024);
+        if (rc || jsmem > optin - 1024) e = cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) {
+        map_join_kernel<<<1, kJoinWarps * 32, jsmem, stream>>>(jp);
+        e = cudaGetLastError();
+        record_launch();
+    }
+    rc = cuda_status(e);
+    if (rc == DNA_OK && positions) {
+        // the single-sequence kernels with every sub-chunk's exact start: no speculation,
+        // no repair; they also write the (same) count
+        dna_plan pl = {};
+        pl.chunk_bytes = (uint32_t)(S / kMapSubs);
+        pl.placement = DNA_PLACE_SMEM_PAIR;
+        rc = scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, &pl, jp.given);
+    }
+    cudaError_t e2 = cudaFreeAsync(mem, stream);
+    if (rc == DNA_OK && e2 != cudaSuccess) rc = cuda_status(e2);
+    return rc;
+}
+
+}  // namespace dnalib

@@ -22,6 +22,7 @@ struct dna_dfa {
     uint32_t reset_entry = 0;
     uint32_t *d_one = nullptr;    // [n_states][4] one-symbol entries, code order A, C, T, G
     uint32_t *d_pair = nullptr;   // [n_states][16] compact pair entries (small automata)
+    bool map_mode = false;        // scans use chunk maps (runs from different states do not meet)
     // resident blocks per SM of each scan kernel variant with this automaton's shared
     // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
     std::atomic<int> per_sm[3][4][2] = {};
@@ -45,9 +46,18 @@ size_t align_up(size_t x, size_t a);
 // Counts kernels launched by the library (reported by dna_profile_read).
 void record_launch(int n = 1);
 
-// The single-sequence scan behind dna_scan / dna_scan_planned.
+// The single-sequence scan behind dna_scan / dna_scan_planned (dispatches to the
+// chunk-map path for automata that need it).
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov);
+// The speculative chunk scan; 'given_start' (per chunk, or null) supplies exact chunk
+// start states, in which case nothing is speculated or repaired.
+int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
+                    uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
+                    const uint32_t *given_start);
+// The chunk-map scan (dna_map.cu); n_states <= 32.
+int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
+                  uint64_t *out_count, uint64_t *out_positions, uint64_t cap);
 
 // Kernel timing: prof_begin records an event on the stream when profiling is enabled
 // (otherwise returns an empty token); prof_end records the closing event.

@@ -586,6 +586,28 @@ namespace dnalib {
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov) {
     if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
+    const uint32_t req = ov ? ov->placement : 0u;
+    if (req > DNA_PLACE_MAP) return DNA_ERR_INVALID_ARG;
+    if (req == DNA_PLACE_MAP || (req == 0 && d->map_mode)) {
+        if (d->n_states > 32 || !d->d_pair) return DNA_ERR_CAPACITY;
+        if (len > (1ull << 40)) return DNA_ERR_INVALID_ARG;
+        int cur_dev = -1;
+        DNA_CUDA(cudaGetDevice(&cur_dev));
+        if (cur_dev != d->device) return DNA_ERR_INVALID_ARG;
+        if (len == 0) {
+            write_zero_kernel<<<1, 1, 0, stream>>>(out_count);
+            record_launch();
+            return cuda_status(cudaGetLastError());
+        }
+        return map_scan_impl(d, seq, len, stream, out_count, out_positions, cap);
+    }
+    return scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, ov, nullptr);
+}
+
+int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
+                    uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
+                    const uint32_t *given_start) {
+    if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
     if (len > (1ull << 40)) return DNA_ERR_INVALID_ARG;
     int cur_dev = -1;
     DNA_CUDA(cudaGetDevice(&cur_dev));
@@ -603,7 +625,9 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     int rc = make_plan(d, total, positions, ov, pl);
     if (rc) return rc;
     const uint64_t nblocks = (uint64_t)pl.grid;
-    const uint32_t pending_cap = (uint32_t)nblocks + 4096u;
+    // every chunk may be pending (automata that converge slowly): the last block then
+    // repairs them all in parallel instead of walking every boundary in order
+    const uint32_t pending_cap = (uint32_t)std::min<uint64_t>(pl.nseg + 16u, 1ull << 31);
     const uint32_t div_cap = 4096;
     Scratch s;
     carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, nullptr);
@@ -615,7 +639,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     ScanParams sp;
     sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
     sp.lookback = pl.lookback; sp.n_states = d->n_states; sp.reset_entry = d->reset_entry;
-    sp.one = d->d_one; sp.pair = d->d_pair;
+    sp.one = d->d_one; sp.pair = d->d_pair; sp.given_start = given_start;
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
     sp.stash = s.stash; sp.nrec = s.nrec; sp.flags = s.flags; sp.fix_delta = s.fix_delta;
     sp.prefetch_tiles = pl.prefetch;
@@ -707,6 +731,28 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
     // within 16 symbols (definite depth <= 16, and in practice most automata on DNA);
     // a known larger depth gets an exact lookback instead
     d->lookback = (d->definite_depth > 16) ? (uint32_t)d->definite_depth : 0u;
+    // automata that are not definite within 64 symbols: do the runs from all states meet
+    // within 16 symbols of typical DNA? Checked on 8 seeded random windows of 256 bases
+    // (small automata only); if not, scans run every chunk from every state (chunk maps)
+    if (d->definite_depth < 0 && n_states <= 32) {
+        uint64_t x = 0x9E3779B97F4A7C15ull;
+        int slow = 0;
+        for (int trial = 0; trial < 8; ++trial) {
+            uint32_t live = n_states == 32 ? 0xFFFFFFFFu : ((1u << n_states) - 1u);
+            int met = -1;
+            for (int k = 0; k < 256 && met < 0; ++k) {
+                x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+                const uint32_t col = (uint32_t)(x >> 62);
+                uint32_t next = 0;
+                for (uint32_t q = 0; q < n_states; ++q)
+                    if (live >> q & 1u) next |= 1u << table[q * 4u + col];
+                live = next;
+                if ((live & (live - 1u)) == 0) met = k + 1;
+            }
+            if (met < 0 || met > 16) ++slow;
+        }
+        d->map_mode = slow > 2;
+    }
     DeviceProps pr = device_props(dev);
     size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
     if (n_states <= max_pair_states(optin, 8)) d->placement = DNA_PLACE_SMEM_PAIR;
@@ -754,6 +800,7 @@ extern "C" int dfa_info(const dna_dfa *d, dna_dfa_info *out) {
     out->placement = d->placement;
     out->accept_start = d->accept0;
     out->device = d->device;
+    out->chunk_maps = d->map_mode ? 1u : 0u;
     return DNA_OK;
 }
 
@@ -862,7 +909,9 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     rc = make_plan(d, total, false, nullptr, pl);
     if (rc) return rc;
     const uint64_t nblocks = (uint64_t)pl.grid;
-    const uint32_t pending_cap = (uint32_t)nblocks + 4096u;
+    // every chunk may be pending (automata that converge slowly): the last block then
+    // repairs them all in parallel instead of walking every boundary in order
+    const uint32_t pending_cap = (uint32_t)std::min<uint64_t>(pl.nseg + 16u, 1ull << 31);
     const uint32_t div_cap = 4096;
     Scratch s;
     carve(s, pl.nseg, nblocks, false, pending_cap, div_cap, nullptr);
@@ -874,7 +923,7 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     ScanParams sp;
     sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
     sp.lookback = pl.lookback; sp.n_states = d->n_states; sp.reset_entry = d->reset_entry;
-    sp.one = d->d_one; sp.pair = d->d_pair;
+    sp.one = d->d_one; sp.pair = d->d_pair; sp.given_start = nullptr;
     sp.spec_start = s.spec_start; sp.last_state = s.last_state; sp.count = s.count;
     sp.stash = nullptr; sp.nrec = nullptr; sp.flags = s.flags; sp.fix_delta = nullptr;
     sp.prefetch_tiles = pl.prefetch;

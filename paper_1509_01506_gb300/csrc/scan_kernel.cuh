@@ -36,6 +36,7 @@ struct ScanParams {
     uint32_t reset_entry;
     const uint32_t *one;    // global one-symbol table
     const uint32_t *pair;   // global compact pair table: next | count << 24
+    const uint32_t *given_start;   // [nseg] exact start state of each chunk, or null (speculate)
     uint32_t *spec_start;   // [nseg] speculated start state
     uint32_t *last_state;   // [nseg] state after the chunk (from the speculated start)
     uint32_t *count;        // [nseg] accepting steps (from the speculated start)
@@ -428,7 +429,10 @@ scan_kernel(ScanParams p) {
 
     // ---- speculated start state: q0, or the state reached from q0 over the lookback window
     uint32_t q = 0;
-    if (has_lookback) {   // the 'lookback' bytes in front of the chunk
+    if (p.given_start) {
+        // the chunk's exact start is known (computed from per-chunk state maps)
+        if (active) q = p.given_start[seg];
+    } else if (has_lookback) {   // the 'lookback' bytes in front of the chunk
         const uint64_t from = b - p.lo > p.lookback ? b - p.lookback : p.lo;
         for (uint64_t off = from; off < b; ++off) q = T.step(q, p.abase[off]) & 0x7FFFFFFFu;
     }

@@ -214,6 +214,51 @@ def test_random_permutation_like_tables():
             assert c == want_c and np.array_equal(p, want_p), (trial, plan)
 
 
+def _permutation_automaton(Q, seed):
+    rng = np.random.default_rng(seed)
+    table = np.stack([rng.permutation(Q) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = (rng.random(Q) < 0.3).astype(np.uint8)
+    acc[int(rng.integers(0, Q))] = 1
+    return table, acc
+
+
+@pytest.mark.parametrize("Q", [2, 5, 17, 32])
+@pytest.mark.parametrize("n,offset", [(1, 0), (4095, 3), (100003, 7), (3 * MiB + 777, 1)])
+def test_chunk_maps_for_automata_that_never_converge(Q, n, offset):
+    """Permutation automata: runs from different states never meet, so dfa_load picks
+    chunk maps (every chunk run from every state, maps composed in order); counts and
+    positions equal the oracle's, across resets and ragged ends."""
+    table, acc = _permutation_automaton(Q, 300 + Q)
+    seq = noisy_markov(400 + n % 97, n) if n > 1000 else synth.uniform(401, n)
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    assert dfa.info().chunk_maps
+    c, p = gpu_run(dfa, to_device(seq, offset), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
+    c2, _ = gpu_run(dfa, to_device(seq, offset), positions=False)
+    assert c2 == want_c
+
+
+def test_chunk_maps_forced_on_a_converging_regex():
+    """The chunk-map path requested through the plan gives the same result as the
+    speculative path on an automaton that does converge."""
+    seq = noisy_markov(31, 5 * MiB + 333)
+    dfa = dna.Dfa.from_regex(synth.CONFIG2_REGEX)
+    assert not dfa.info().chunk_maps
+    check("regex", synth.CONFIG2_REGEX, seq, offset=9, plan=dict(placement=4))
+    check("regex", synth.CONFIG2_REGEX, seq, offset=0, plan=dict(placement=4), positions=False)
+
+
+def test_chunk_maps_full_size():
+    """64 MiB against an 8-state permutation automaton (never converging)."""
+    table, acc = _permutation_automaton(8, 77)
+    seq = noisy_markov(78, 64 * MiB)
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    c, p = gpu_run(dfa, to_device(seq), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
+
+
 def test_positions_capacity_smaller_than_count():
     seq = synth.uniform(5, 2 * MiB)
     t, a = oracle.compile_regex("AC")
