@@ -441,6 +441,22 @@ def bench_plain_configs(dna, torch, stream, peak):
                                 "matches": int(cnt.item()), "output": "count + positions",
                                 "note": "launch-bound: two kernels of about 10 us each"}
     del d
+    # an automaton whose runs never meet (an 8-state permutation table): chunk maps
+    full, _ = synth.plain_markov(256 * MiB)
+    rng = np.random.Generator(np.random.PCG64(8))
+    table = np.stack([rng.permutation(8) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = (rng.random(8) < 0.25).astype(np.uint8)
+    acc[0] = 0
+    acc[int(rng.integers(1, 8))] = 1
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    d = torch.from_numpy(full).cuda()
+    fn = lambda: dna.scan(dfa, d, stream=stream, out_count=cnt)
+    ms = timed(fn, 10)
+    out["nonconverging_256MiB_perm8"] = {
+        "bytes": int(full.size), "ms_per_step": ms, "gbs": full.size / (ms * 1e-3) / 1e9,
+        "matches": int(cnt.item()), "chunk_maps": bool(dfa.info().chunk_maps), "output": "count",
+        "note": "runs from different states never meet: every chunk is run from all 8 states"}
+    del d, full
     seq, kmers = synth.plain_large()
     dfa = dna.Dfa.from_kmers(kmers)
     info = dfa.info()

@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
     __syncthreads();
     const uint32_t c = blockIdx.x * kMapWarps + warp;
     if (c >= p.n_chunks) return;   // warp-uniform; no barrier follows
+    __shared__ __align__(16) uint32_t ys_all[kMapWarps][32];
+    uint32_t *ys = ys_all[warp];
 
     OneTable T;
     T.t = one_s;
@@ -105,34 +107,40 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
             const bool full = ro >= from && ro + kTile <= to;
             bool done = false;
             if (full) {
-                uint32_t w[32];
+                // lane k decodes word k once for the whole warp: its pair codes (y, read
+                // back by every lane) and the base check (voted)
+                const uint32_t wk = *reinterpret_cast<const uint32_t *>(row + 4 * lane);
+                const uint32_t xk = wk & 0x06060606u;
+                ys[lane] = mad_lo(xk, 65u, 0u);
+                const uint32_t zk = xk | (xk >> 4);
+                const bool bad = ((__byte_perm(p.lut_lo, p.lut_hi, __byte_perm(zk, 0, 0x0020)) ^ wk) & 0xDFDFDFDFu) != 0;
+                const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
+                __syncwarp();
+                if (!any_bad) {
+                    uint32_t acc = 0, rc = 0, c2 = cur;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(row + 16 * i);
-                    w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
-                }
-                uint32_t acc = 0, err = 0, rc = 0, c2 = cur;
+                    for (int k4 = 0; k4 < 8; ++k4) {
+                        const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
+                        const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const uint32_t x = w[k] & 0x06060606u;
-                    const uint32_t y = mad_lo(x, 65u, 0u);
-                    const uint32_t e1 = lds_u32(mux_pair(c2, y));
-                    const uint32_t e2 = lds_u32(mux_pair(e1, y >> 16));
-                    acc = mad_lo(e1, p.k1, acc);
-                    acc = mad_lo(e2, p.k1, acc);
-                    c2 = e2;
-                    if (k % 3 == 2 || k == 31) {
-                        rc = mad_hi(acc, p.k5, rc);
-                        acc = 0;
+                        for (int i = 0; i < 4; ++i) {
+                            const int k = 4 * k4 + i;
+                            const uint32_t e1 = lds_u32(mux_pair(c2, yv[i]));
+                            const uint32_t e2 = lds_u32(mux_pair(e1, yv[i] >> 16));
+                            acc = mad_lo(e1, p.k1, acc);
+                            acc = mad_lo(e2, p.k1, acc);
+                            c2 = e2;
+                            if (k % 3 == 2 || k == 31) {
+                                rc = mad_hi(acc, p.k5, rc);
+                                acc = 0;
+                            }
+                        }
                     }
-                    const uint32_t z = x | (x >> 4);
-                    err |= __byte_perm(p.lut_lo, p.lut_hi, __byte_perm(z, 0, 0x0020)) ^ w[k];
-                }
-                if ((err & 0xDFDFDFDFu) == 0) {
                     cnt += rc;
                     cur = c2 & 0x3FFFFu;
                     done = true;
                 }
+                __syncwarp();   // ys is rewritten by the next row
             }
             if (!done) {
                 // reset bytes or a sequence edge in this row: byte by byte
@@ -257,7 +265,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     mp.k1 = 1u; mp.k5 = 32u; mp.lut_lo = 0x00630061u; mp.lut_hi = 0x00670074u;
     const size_t msmem = (size_t)kMapWarps * 2 * kMapTile + 32 * 16 + 2048 + (size_t)d->n_states * kPairRowBytes;
     const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
-    int rc = ensure_smem_optin((const void *)map_kernel, d->device, optin - 1024);
+    int rc = ensure_smem_optin((const void *)map_kernel, d->device, optin - 4096);   // static: about 3 KB
     cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
     if (e == cudaSuccess) {
         const ProfToken tk = prof_begin(stream);
