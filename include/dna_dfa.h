@@ -350,6 +350,28 @@ uint64_t dna_server_now_ns(void);
  * the server. NULL is ignored. */
 void dna_server_free(dna_server *server);
 
+/*
+ * dna_fasta_parse -- host FASTA ingest (no GPU needed). A record is a '>' header line
+ * (the '>' at the start of a line) and the sequence lines after it; text before the
+ * first header is an unnamed record. Line breaks (LF, CR LF), spaces and tabs are
+ * dropped and each record's remaining bytes are appended, unchanged, to 'out': letters
+ * keep their case and non-base letters (N, IUPAC codes) stay and act as reset symbols in
+ * the scans. Records are concatenated without separators; scan each record's span (for
+ * instance as one dna_batch with a pointer per record) so that no match crosses records.
+ *   text, len      the file contents (host).
+ *   out, cap       host buffer for the sequence bytes, or NULL with cap = 0 to size only.
+ *   out_len        receives the number of sequence bytes.
+ *   rec_off        NULL, or uint64 [rec_cap]: record r is out[rec_off[r], rec_off[r+1]);
+ *                  needs n_records + 1 entries.
+ *   hdr_span       NULL, or uint64 [2 * rec_cap]: record r's header text is
+ *                  text[hdr_span[2r], hdr_span[2r+1]) (empty for an unnamed record).
+ *   n_records      receives the number of records.
+ * Returns DNA_ERR_CAPACITY when out or rec_off is too small (the counts are still set).
+ * The paper reads GenBank FASTA files (Sec. IV-A); this is the matching ingest.
+ */
+int dna_fasta_parse(const char *text, uint64_t len, uint8_t *out, uint64_t cap, uint64_t *out_len,
+                    uint64_t *rec_off, uint64_t *hdr_span, uint32_t rec_cap, uint32_t *n_records);
+
 /* dna_status_string -- a static description of a status code. */
 const char *dna_status_string(int status);
 

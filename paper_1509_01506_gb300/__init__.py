@@ -26,7 +26,7 @@ EXPORTED = [
     "dna_scan_count_static", "dna_scan_host",
     "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
     "dna_server_create", "dna_server_submit", "dna_server_poll", "dna_server_drain",
-    "dna_server_stats", "dna_server_now_ns", "dna_server_free",
+    "dna_server_stats", "dna_server_now_ns", "dna_server_free", "dna_fasta_parse",
     "dna_status_string", "dna_compile_regex", "dna_compile_kmers", "dna_free_host",
     "dna_profile_enable", "dna_profile_read",
 ]
@@ -148,6 +148,9 @@ def lib():
         L.dna_server_now_ns.restype = u64
         L.dna_server_free.argtypes = [p]
         L.dna_server_free.restype = None
+        L.dna_fasta_parse.argtypes = [ctypes.c_char_p, u64, p, u64, ctypes.POINTER(u64), p, p, u32,
+                                      ctypes.POINTER(u32)]
+        L.dna_fasta_parse.restype = i32
         L.dna_scan_batch.argtypes = [p, u32, p, p, u32, p, p]
         L.dna_scan_batch.restype = i32
         L.dna_status_string.argtypes = [i32]
@@ -207,6 +210,23 @@ def compile_kmers(kmers):
                                    ctypes.byref(tp), ctypes.byref(ap), ctypes.byref(n)),
            "compile_kmers")
     return _take_table(tp, ap, n.value)
+
+
+def fasta_parse(text: bytes):
+    """dna_fasta_parse: (sequence bytes as a uint8 array, record offsets [n+1], headers).
+    Record r is seq[offsets[r]:offsets[r+1]]."""
+    L = lib()
+    n_out, n_rec = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(L.dna_fasta_parse(text, len(text), None, 0, ctypes.byref(n_out), None, None, 0,
+                             ctypes.byref(n_rec)), "dna_fasta_parse")
+    seq = np.empty(n_out.value, dtype=np.uint8)
+    off = np.empty(n_rec.value + 1, dtype=np.uint64)
+    hdr = np.empty(2 * (n_rec.value + 1), dtype=np.uint64)
+    _check(L.dna_fasta_parse(text, len(text), seq.ctypes.data, seq.size, ctypes.byref(n_out),
+                             off.ctypes.data, hdr.ctypes.data, off.size, ctypes.byref(n_rec)),
+           "dna_fasta_parse")
+    headers = [text[int(hdr[2 * r]):int(hdr[2 * r + 1])].decode(errors="replace") for r in range(n_rec.value)]
+    return seq, off.astype(np.int64), headers
 
 
 def definite_depth(table) -> int:

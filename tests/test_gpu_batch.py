@@ -176,3 +176,37 @@ def test_batch_full_size_sampled():
             dna.scan_ptr(dfas[k], starts[s], lens[s], out.data_ptr(), int(torch.cuda.current_stream().cuda_stream))
             torch.cuda.synchronize()
             assert int(out.item()) == got[s, k]
+
+
+def test_fasta_records_scanned_as_a_batch():
+    """FASTA ingest: records parsed on the host, copied once, scanned as one batch (a
+    pointer per record); each record's counts equal the oracle's on that record alone."""
+    rng = np.random.default_rng(12)
+    parts, recs = [], []
+    for r in range(5):
+        s = synth.markov2(500 + r, int(rng.integers(10_000, 300_000)))
+        recs.append(s)
+        lines = [bytes(s[i:i + 60]) for i in range(0, s.size, 60)]
+        parts.append(b">rec%d sample\n" % r + b"\n".join(lines) + b"\n")
+    seq, off, hdr = dna.fasta_parse(b"".join(parts))
+    assert hdr == ["rec%d sample" % r for r in range(5)]
+    d = torch.from_numpy(seq).cuda()
+    ptrs = [d.data_ptr() + int(off[r]) for r in range(5)]
+    lens = [int(off[r + 1] - off[r]) for r in range(5)]
+    pats = [("regex", synth.CONFIG2_REGEX), ("regex", "TATAAA")]
+    got = dna.Batch(lib_dfas(pats), ptrs, lens=lens).run()
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), oracle_counts(pats, recs))
+
+
+def test_regex_dna_per_expression_counts():
+    """The paper's regex-dna output: one count per expression of Table V (E1..E9, each a
+    pattern | its reverse complement) for each input, from one batch of 9 automata."""
+    seqs = [synth.markov2(600 + i, n) for i, n in enumerate((1_000_003, 250_000, 4096))]
+    for s in seqs:
+        synth.overlay_runs(s, 7, 0.05, 400.0, "lower")
+    dseqs, keep = to_device_list(seqs)
+    pats = [("regex", e) for e in synth.REGEX_DNA_TABLE_V]
+    got = dna.Batch(lib_dfas(pats), dseqs).run()
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), oracle_counts(pats, seqs))

@@ -119,3 +119,56 @@ def test_pack_accept_layout():
     a[[0, 9, 18]] = 1
     m = dna.pack_accept(a)
     assert m.tolist() == [1, 2, 4]
+
+
+# ------------------------------------------------------------------ FASTA ingest
+
+def _fasta_reference(text: bytes):
+    """Plain reading of FASTA: records start at '>' lines; sequence lines are joined with
+    line breaks, spaces and tabs removed; text before the first header is a record."""
+    recs, hdrs, cur = [], [], None
+    for line in re.split(rb"\r\n|\n|\r", text):
+        if line.startswith(b">"):
+            cur = bytearray()
+            recs.append(cur)
+            hdrs.append(line[1:].decode())
+            continue
+        body = line.replace(b" ", b"").replace(b"\t", b"")
+        if body and cur is None:
+            cur = bytearray()
+            recs.append(cur)
+            hdrs.append("")
+        if cur is not None:
+            cur.extend(body)
+    return recs, hdrs
+
+
+def test_fasta_parse_against_a_plain_reading():
+    text = (b"ACGTN\n"                                        # unnamed first record
+            b">chr1 test record\r\nACGTacgtNNNN\r\nTTTA CCC\r\n\r\n"
+            b">chr2\nGATTACA\n\n>empty\n>chr3\rACGT\rAC\tGT\n>x\nA>C\n")
+    seq, off, hdr = dna.fasta_parse(text)
+    recs, want_hdr = _fasta_reference(text)
+    assert hdr == want_hdr
+    assert len(off) == len(recs) + 1
+    for r, rec in enumerate(recs):
+        assert bytes(seq[off[r]:off[r + 1]]) == bytes(rec), r
+    assert int(off[-1]) == seq.size == sum(len(r) for r in recs)
+
+
+def test_fasta_parse_capacity_and_sizing():
+    lib = dna.lib()
+    text = b">a\nACGT\n>b\nGG\n"
+    n_out, n_rec = ctypes.c_uint64(), ctypes.c_uint32()
+    assert lib.dna_fasta_parse(text, len(text), None, 0, ctypes.byref(n_out), None, None, 0,
+                               ctypes.byref(n_rec)) == 0
+    assert (n_out.value, n_rec.value) == (6, 2)
+    small = (ctypes.c_uint8 * 3)()
+    off = (ctypes.c_uint64 * 3)()
+    assert lib.dna_fasta_parse(text, len(text), small, 3, ctypes.byref(n_out), off, None, 3,
+                               ctypes.byref(n_rec)) == -3
+    assert n_out.value == 6
+    off2 = (ctypes.c_uint64 * 2)()
+    big = (ctypes.c_uint8 * 8)()
+    assert lib.dna_fasta_parse(text, len(text), big, 8, ctypes.byref(n_out), off2, None, 2,
+                               ctypes.byref(n_rec)) == -3
