@@ -543,6 +543,17 @@ def main():
     torch.cuda.synchronize()
     dna.profile_enable(False)
     prof = dna.profile_read(reset=True)
+    ns = max(1, prof["conv_scans"])
+    chunks = prof["conv_chunks"] / ns
+    speculation = {
+        "chunks_per_scan": chunks,
+        "wrong_start_repaired_in_block": prof["conv_inblock"] / ns,
+        "block_first_wrong_start": prof["conv_blockfirst"] / ns,
+        "repaired_by_last_block": prof["conv_pending"] / ns,
+        "last_state_changed": prof["conv_diverged"] / ns,
+        "cascade_walks": prof["conv_cascade"] / ns,
+        "wrong_start_fraction": (prof["conv_inblock"] + prof["conv_blockfirst"] + prof["conv_pending"]) / ns / max(1.0, chunks),
+        "note": "q0 speculation; a wrong start is repaired where the runs meet (converging point)"}
 
     # ---- end to end through dna_scan_host: pinned host sequence in, count and positions
     # back in pinned host memory, every step (the call returns when they are on the host)
@@ -611,6 +622,7 @@ def main():
                        "parallelism": f"independent sequences on {world} GPU(s)",
                        "e2e_steps": e2e_steps},
             "roofline": roofline,
+            "speculation": speculation,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": n,
                     "d2h_bytes_per_step": 8 + 8 * n_matches, "ms_per_step": e2e_ms,

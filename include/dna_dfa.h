@@ -409,6 +409,15 @@ typedef struct {
     uint64_t batch_kernel_calls;
     double   ingest_kernel_ms;  /* batched ingest (2-bit packing) kernel */
     uint64_t ingest_kernel_calls;
+    /* speculation statistics of the profiled chunk scans (Sec. III-A, III-B.3): */
+    uint64_t conv_scans;        /* scans counted */
+    uint64_t conv_chunks;       /* chunks */
+    uint64_t conv_inblock;      /* chunks whose speculated start was wrong and whose runs met
+                                   within their first 16 bytes (repaired in the block) */
+    uint64_t conv_pending;      /* chunks whose runs did not meet there (repaired by the last block) */
+    uint64_t conv_blockfirst;   /* first chunks of blocks joined with a wrong start */
+    uint64_t conv_diverged;     /* repairs that changed a chunk's last state */
+    uint64_t conv_cascade;      /* chunks re-walked by the cascade */
 } dna_profile_t;
 
 void dna_profile_enable(int enable);

@@ -57,7 +57,11 @@ class _Profile(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64),
                 ("emit_kernel_ms", ctypes.c_double), ("emit_kernel_calls", ctypes.c_uint64),
                 ("batch_kernel_ms", ctypes.c_double), ("batch_kernel_calls", ctypes.c_uint64),
-                ("ingest_kernel_ms", ctypes.c_double), ("ingest_kernel_calls", ctypes.c_uint64)]
+                ("ingest_kernel_ms", ctypes.c_double), ("ingest_kernel_calls", ctypes.c_uint64),
+                ("conv_scans", ctypes.c_uint64), ("conv_chunks", ctypes.c_uint64),
+                ("conv_inblock", ctypes.c_uint64), ("conv_pending", ctypes.c_uint64),
+                ("conv_blockfirst", ctypes.c_uint64), ("conv_diverged", ctypes.c_uint64),
+                ("conv_cascade", ctypes.c_uint64)]
 
 
 class _BatchOpts(ctypes.Structure):

@@ -67,6 +67,9 @@ struct ProfToken {
 };
 ProfToken prof_begin(cudaStream_t s);
 void prof_end(ProfToken t, cudaStream_t s, int which);
+// Convergence counters of one scan (control words 1..5 of its scratch), copied to the
+// host and summed when profiling is enabled.
+void prof_conv(cudaStream_t s, const uint32_t *dev_ctrl, uint64_t nseg);
 void profile_set(int on);
 void profile_collect(dna_profile_t *out, int reset);
 

@@ -419,6 +419,31 @@ void prof_end(ProfToken t, cudaStream_t s, int which) {
     g_prof_pending.push_back({t.a, t.b, which});
 }
 
+struct ConvRec { uint32_t *host; cudaEvent_t ev; uint64_t nseg; };
+static std::vector<ConvRec> g_conv_pending, g_conv_free;
+static uint64_t g_conv[7] = {};   // scans, chunks, in-block, pending, block-first, diverged, cascade
+
+void prof_conv(cudaStream_t s, const uint32_t *dev_ctrl, uint64_t nseg) {
+    if (g_profile.load(std::memory_order_relaxed) == 0) return;
+    ConvRec r{nullptr, nullptr, nseg};
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_conv_free.empty()) { r.host = g_conv_free.back().host; r.ev = g_conv_free.back().ev; g_conv_free.pop_back(); }
+    }
+    if (!r.host) {
+        if (cudaMallocHost(&r.host, 32) != cudaSuccess) return;
+        if (cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) { cudaFreeHost(r.host); return; }
+    }
+    if (cudaMemcpyAsync(r.host, dev_ctrl, 32, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaEventRecord(r.ev, s) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_conv_free.push_back(r);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_conv_pending.push_back(r);
+}
+
 void profile_set(int on) { g_profile.store(on ? 1 : 0); }
 
 void profile_collect(dna_profile_t *out, int reset) {
@@ -441,8 +466,29 @@ void profile_collect(dna_profile_t *out, int reset) {
     out->batch_kernel_calls = g_prof_calls[PROF_BATCH];
     out->ingest_kernel_ms = g_prof_ms[PROF_INGEST];
     out->ingest_kernel_calls = g_prof_calls[PROF_INGEST];
+    for (auto &r : g_conv_pending) {
+        if (cudaEventSynchronize(r.ev) == cudaSuccess) {
+            g_conv[0] += 1;
+            g_conv[1] += r.nseg;
+            g_conv[2] += r.host[3];   // in-block repairs
+            g_conv[3] += r.host[1];   // pending (last block)
+            g_conv[4] += r.host[4];   // block-first chunks with a wrong start
+            g_conv[5] += r.host[2];   // diverged
+            g_conv[6] += r.host[5];   // cascade walks
+        }
+        g_conv_free.push_back(r);
+    }
+    g_conv_pending.clear();
+    out->conv_scans = g_conv[0];
+    out->conv_chunks = g_conv[1];
+    out->conv_inblock = g_conv[2];
+    out->conv_pending = g_conv[3];
+    out->conv_blockfirst = g_conv[4];
+    out->conv_diverged = g_conv[5];
+    out->conv_cascade = g_conv[6];
     if (reset) {
         for (int k = 0; k < PROF_N; ++k) { g_prof_ms[k] = 0; g_prof_calls[k] = 0; }
+        for (int k = 0; k < 7; ++k) g_conv[k] = 0;
         g_launches.store(0);
     }
 }
@@ -563,7 +609,7 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
            uint32_t div_cap, uint8_t *base) {
     size_t off = 0;
     auto take = [&](size_t bytes) { uint8_t *q = base ? base + off : nullptr; off = align_up(off + bytes, 256); return q; };
-    s.ctrl = (uint32_t *)take(16);
+    s.ctrl = (uint32_t *)take(32);
     s.cta_sum = (unsigned long long *)take(nblocks * 8);
     s.cta_off = (unsigned long long *)take(nblocks * 8);
     s.block_head = (uint4 *)take(nblocks * 16);
@@ -634,7 +680,7 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     void *mem = nullptr;
     DNA_CUDA(cudaMallocAsync(&mem, s.bytes, stream));
     carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, (uint8_t *)mem);
-    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 16, stream);
+    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 32, stream);
 
     ScanParams sp;
     sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
@@ -646,7 +692,7 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
     sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
-    sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
+    sp.k1 = 1u; sp.k5 = 1u << 5;
     sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
 
     const ProfToken tok = e == cudaSuccess ? prof_begin(stream) : ProfToken{};
@@ -656,6 +702,7 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
         record_launch();
     }
     prof_end(tok, stream, PROF_SCAN);
+    if (e == cudaSuccess) prof_conv(stream, s.ctrl, pl.nseg);
     if (e == cudaSuccess && positions) {
         EmitParams ep;
         ep.abase = abase; ep.lo = shift; ep.hi = total; ep.seg_bytes = pl.seg_bytes; ep.nseg = pl.nseg;
@@ -918,7 +965,7 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     if (s.bytes > kStaticScratchBytes) return DNA_ERR_CAPACITY;
     carve(s, pl.nseg, nblocks, false, pending_cap, div_cap, (uint8_t *)base);
     // the counters the kernel expects at zero; everything else is written before it is read
-    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 16, stream);
+    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 32, stream);
     if (e != cudaSuccess) return cuda_status(e);
     ScanParams sp;
     sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
@@ -930,7 +977,7 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
     sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
-    sp.k1 = 1u; sp.k16 = 1u << 16; sp.k5 = 1u << 5; sp.k28 = 1u << 28;
+    sp.k1 = 1u; sp.k5 = 1u << 5;
     sp.lut_lo = 0x00630061u; sp.lut_hi = 0x00670074u;
     scan_fn(pl.mode, pl.warps, false)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);
     record_launch();

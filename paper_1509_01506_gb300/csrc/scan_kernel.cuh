@@ -45,7 +45,9 @@ struct ScanParams {
     uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
     uint8_t *flags;         // [nseg] kFlag* bits for the extraction pass
     uint32_t *fix_delta;    // [nseg] count offset shift of a kFlagFixed chunk's later rows
-    uint32_t *ctrl;         // [4] zeroed before launch: finish ticket, pending, diverged, 0
+    uint32_t *ctrl;         // [8] zeroed before launch: finish ticket, pending, diverged, then
+                            //   counters: chunks repaired in-block at the converging point,
+                            //   block-first chunks joined with a wrong start, cascade walks
     uint32_t *pending;      // chunks whose 16-byte in-block repair did not converge (the last
     uint32_t pending_cap;   //   block repairs them; it joins every block's first chunk anyway)
     uint32_t *div_list;     // [div_cap] chunks whose last state changed in a repair
@@ -54,9 +56,9 @@ struct ScanParams {
     unsigned long long *cta_off;   // [grid] exclusive prefix of cta_sum (for extraction)
     uint4 *block_head;             // [grid] first 16 bytes of each block's first chunk
     uint64_t *out_count;
-    // 1, 2^16, 2^5, 2^28 passed at run time so the compiler keeps the multiplies that
-    // use them (adds and shifts) on the FMA pipe instead of turning them into ALU ops
-    uint32_t k1, k16, k5, k28;
+    // 1 and 2^5 passed at run time so the compiler keeps the multiplies that use them
+    // (adds and shifts) on the FMA pipe instead of turning them into ALU ops
+    uint32_t k1, k5;
     // lowercase letters selected by the codes (a, c at bytes 0, 2; t, g at bytes 4, 6),
     // passed at run time so that they stay in registers across the unrolled row loop
     uint32_t lut_lo, lut_hi;
@@ -225,6 +227,7 @@ __device__ void finalize_block(const ScanParams &p, const OneTable &T, unsigned 
         const uint32_t a = p.last_state[c - 1];
         const uint32_t s = p.spec_start[c];
         if (a == s) return;
+        if (head) atomicAdd(&p.ctrl[4], 1u);
         const uint32_t old_last = p.last_state[c];
         const Repair r = repair_chunk(p, T, c, a, s, head);
         apply_repair(p, c, a, r, cpb, sums);
@@ -273,6 +276,7 @@ __device__ void finalize_block(const ScanParams &p, const OneTable &T, unsigned 
                     if (k >= p.nseg || cur == p.spec_start[k]) { walked = k; break; }
                     const Repair r = repair_chunk(p, T, k, cur, p.spec_start[k], nullptr);
                     apply_repair(p, k, cur, r, cpb, sums);
+                    atomicAdd(&p.ctrl[5], 1u);
                     p.flags[k] = kFlagRescan;   // its records follow a start that was not the true one
                     cur = r.last;
                     ++k;
@@ -317,6 +321,7 @@ scan_kernel(ScanParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint32_t warp_last[WARPS];
     __shared__ uint4 head_s[WARPS * 32];   // each chunk's first 16 bytes, for the repair
+    __shared__ uint32_t s_nfix;            // chunks of this block repaired at their converging point
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
@@ -539,6 +544,7 @@ scan_kernel(ScanParams p) {
     // the true start of a chunk is the last state of the chunk before it, which the lane
     // to the left (or, for lane 0, the previous warp's lane 31) has just computed
     if (lane == 31) warp_last[warp] = last;
+    if (threadIdx.x == 0) s_nfix = 0;
     __syncthreads();
     uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, last, 1);
     if (lane == 0) prev = warp > 0 ? warp_last[warp - 1] : 0u;
@@ -596,6 +602,11 @@ scan_kernel(ScanParams p) {
         const uint32_t k = atomicAdd(&p.ctrl[1], 1u);
         if (k < p.pending_cap) p.pending[k] = (uint32_t)seg;
     }
+    {   // convergence statistics: chunks whose speculated start was repaired in-block
+        // (added up in shared memory; one global add per block after its ticket)
+        const uint32_t nfix = __popc(__ballot_sync(0xFFFFFFFFu, fixed));
+        if (lane == 0 && nfix) atomicAdd(&s_nfix, nfix);
+    }
     __threadfence();   // this thread's results are visible before the block's ticket
     // the extraction kernel (launched as a programmatic dependent) may be scheduled once
     // every block has got here; it still waits for this grid to finish before reading
@@ -613,6 +624,7 @@ scan_kernel(ScanParams p) {
         p.cta_sum[blockIdx.x] = t;
         __threadfence();
         is_last = atomicAdd(&p.ctrl[0], 1u) == gridDim.x - 1;
+        if (s_nfix) atomicAdd(&p.ctrl[3], s_nfix);
     }
     __syncthreads();
     if (!is_last) return;
