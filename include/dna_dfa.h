@@ -70,8 +70,10 @@ typedef struct dna_dfa dna_dfa; /* opaque; its tables live in device memory */
  *   out         receives the handle; the library owns it until dfa_free.
  * The table is copied (the caller may free its buffers on return). dfa_load also
  * analyses the automaton on the host (its definite depth: the smallest m such that
- * any m symbols bring every state to one state, when m <= 64) and picks the
- * speculation lookback and the table placement used by the scans.
+ * any m symbols bring every state to one state, when m <= 64; and, for automata of at
+ * most 32 states that are not definite, whether runs from all states meet within 16
+ * symbols of random DNA) and picks the speculation lookback, the table placement and
+ * whether scans use chunk maps (DNA_PLACE_MAP).
  * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_NOMEM, DNA_ERR_CUDA, DNA_ERR_NO_DEVICE.
  */
 int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t *accept_mask,
@@ -127,7 +129,11 @@ int dfa_analyze(const uint32_t *table, uint32_t n_states, int32_t *definite_dept
  *   positions_capacity  number of uint64 slots at out_positions.
  * Scratch: the call allocates stream-ordered device scratch (cudaMallocAsync) sized
  * O(len / chunk) and frees it on the same stream.
- * Errors: DNA_ERR_INVALID_ARG (synchronous), DNA_ERR_NOMEM, DNA_ERR_CUDA.
+ * Kernels: one chunk-scan kernel (speculation, chunk scan, join) and, with positions,
+ * one extraction kernel; automata using chunk maps run a map kernel and a join kernel
+ * first (and, with positions, the chunk-scan kernels from the exact chunk starts).
+ * Errors: DNA_ERR_INVALID_ARG (synchronous), DNA_ERR_NOMEM, DNA_ERR_CUDA,
+ * DNA_ERR_CAPACITY (a plan's placement the automaton does not fit).
  */
 int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t stream,
              uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity);
@@ -166,6 +172,8 @@ int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64_t len, dna
  *   calls that overlap on the GPU (different streams, or no ordering between them)
  *   race on it and give wrong counts. Order the calls, e.g. issue them on one stream.
  *   No cudaMalloc, cudaFree or allocating library routine is called.
+ *   Automata that dna_scan runs with chunk maps are scanned here with speculation and
+ *   repair (exact, but slow when runs from different states never meet).
  * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_CAPACITY, DNA_ERR_CUDA.
  */
 int dna_scan_count_static(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
