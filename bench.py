@@ -170,7 +170,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import synth
-    n = min(args.bytes, 64 * MiB)
+    # a bounded sample per step, so that the whole run stays near half a minute of oracle
+    # work (about 12 GB at the oracle's 0.3-0.5 GB/s) whatever --steps is
+    n = int(min(args.bytes, 64 * MiB, max(256 * 1024, 12e9 // max(1, args.steps))))
     seq, pattern = synth.plain_markov(args.bytes)
     seq = seq[:n]
     import oracle
@@ -187,9 +189,9 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": {"workload": WORKLOAD, "bytes_per_step": n,
-                                        "sample": f"first {n // MiB} MiB of the workload per step"},
+                                        "sample": f"first {n} bytes of the workload per step"},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n // MiB} MiB of the 256 MiB sequence per step"},
+                         "sample": f"first {n} bytes of the 256 MiB sequence per step"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
