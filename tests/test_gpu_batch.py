@@ -210,3 +210,23 @@ def test_regex_dna_per_expression_counts():
     got = dna.Batch(lib_dfas(pats), dseqs).run()
     torch.cuda.synchronize()
     assert np.array_equal(got.cpu().numpy(), oracle_counts(pats, seqs))
+
+
+def test_batch_with_a_chunk_map_automaton(mixed):
+    """A never-converging automaton in a batch goes to the single-sequence path, which
+    uses chunk maps; its column equals the oracle's."""
+    pats, seqs, dseqs, _, want, dfas = mixed
+    rng = np.random.default_rng(92)
+    table = np.stack([rng.permutation(9) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = (np.arange(9) % 4 == 1).astype(np.uint8)
+    perm = dna.Dfa(table, dna.pack_accept(acc))
+    assert perm.info().chunk_maps
+    b = dna.Batch(dfas + [perm], dseqs)
+    assert b.info().n_slow == 3
+    got = b.run()
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    b.free()
+    assert np.array_equal(got[:, :-1], want)
+    col = [oracle.run(table.astype(np.int32), acc, s, positions=False)[0] for s in seqs]
+    assert got[:, -1].tolist() == col

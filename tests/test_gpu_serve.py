@@ -113,3 +113,28 @@ def test_request_larger_than_the_cap_fails_alone(workload):
             s2.submit((pinned.data_ptr(), 100), 5)
         finally:
             s2.free()
+
+
+def test_request_loop_with_a_chunk_map_automaton(workload):
+    """A never-converging automaton (chunk maps) served among ordinary ones."""
+    pinned, lens, offs, dfa_idx, want, dfas = workload
+    rng = np.random.default_rng(91)
+    table = np.stack([rng.permutation(6) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = np.array([0, 1, 0, 0, 1, 0], np.uint8)
+    perm = dna.Dfa(table, dna.pack_accept(acc))
+    assert perm.info().chunk_maps
+    srv = dna.Server(dfas + [perm], slots=4)
+    base = pinned.data_ptr()
+    payload = pinned.numpy()
+    ids = {}
+    for i in range(30):
+        o, n = int(offs[i]), int(lens[i])
+        ids[srv.submit((base + o, n), len(dfas))] = (o, n)
+    srv.drain()
+    comps = srv.poll(64)
+    srv.free()
+    assert len(comps) == 30
+    for c in comps:
+        o, n = ids[c["id"]]
+        assert c["status"] == 0
+        assert c["count"] == oracle.run(table.astype(np.int32), acc, payload[o:o + n], positions=False)[0]
