@@ -579,6 +579,21 @@ def main():
     assert c_host == n_matches
     e2e_ms = shard.max_over_ranks(e2e_ms, device="cuda")
     e2e_value = n * world / (e2e_ms * 1e-3) / 1e9
+    # the bound of the end-to-end number: the host link, timed as a plain copy of the same
+    # pinned sequence into device memory (copy engine, CUDA events on the same stream)
+    link_dst = torch.empty(n, dtype=torch.uint8, device="cuda")
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    link_ms = []
+    for r in range(6):
+        l0.record(stream)
+        link_dst.copy_(host_in, non_blocking=True)
+        l1.record(stream)
+        l1.synchronize()
+        if r:
+            link_ms.append(l0.elapsed_time(l1))
+    del link_dst
+    link_gbs = n / (statistics.median(link_ms) * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel (the chunk scan), timed live with events
     peak, peak_kind = load_peaks()
@@ -628,7 +643,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": n,
                     "d2h_bytes_per_step": 8 + 8 * n_matches, "ms_per_step": e2e_ms,
-                    "api": "dna_scan_host (pinned host buffers, synchronous)"},
+                    "api": "dna_scan_host (pinned host buffers, synchronous)",
+                    "host_link_gbs": link_gbs, "frac_of_host_link": e2e_value / world / link_gbs,
+                    "host_link_source": "cudaMemcpyAsync of the same pinned 256 MiB to the device, median of 5"},
             "gpu_launches": launches,
             "plain_configs": plain_configs,
             "batched": batched,
