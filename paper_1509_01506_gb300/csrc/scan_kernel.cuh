@@ -455,6 +455,13 @@ scan_kernel(ScanParams p) {
         t_full0 = b < p.lo ? 1u : 0u;
     }
     const uint32_t lut_lo = p.lut_lo, lut_hi = p.lut_hi;
+    // run-time 2 and 16 (from k1 and k5), so the multiplies by them stay multiplies
+    const uint32_t k2 = p.k1 << 1, k16 = p.k5 >> 1;
+    // shared address of the one-symbol table; when it is 256-aligned its low byte is free
+    // for a code's column offset (otherwise every row is walked by row_bytes_reg)
+    const uint32_t one_addr = smem_base + (uint32_t)WARPS * kStages * kStageBytes;
+    const bool one_fast = (one_addr & 0xFFu) == 0;
+    const uint32_t reset_e = p.reset_entry;
     for (uint32_t t = 0; t < ntiles; ++t) {
         cp_async_wait<0>();
         __syncwarp();   // tile t of all 32 rows is visible to the warp
@@ -530,10 +537,40 @@ scan_kernel(ScanParams p) {
             }
         } else {
             uint32_t before = cnt, qs = q;
-            q = full ? row_bytes_reg(T, qs, w, cnt)
-                     : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
-                                        row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
-            if (POS && cnt != before) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, before); }
+            bool done = false;
+            if (MODE == MODE_ONE_SMEM && full && one_fast) {
+                // One lookup per byte. The shared address of the next entry is entry * 16 +
+                // table base + code * 4: the product drops the accept bit (bit 31) and
+                // leaves the next state's row offset, so a base costs one multiply-add, one
+                // load and one multiply-high (count += entry >> 31). A reset byte (its
+                // lowercase form is not that of its code's letter) takes the reset entry in
+                // place of the loaded one, without a branch.
+                uint32_t e = q, rc = 0, err = 0;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const uint32_t x = w[k] & 0x06060606u;
+                    const uint32_t v = mad_lo(x, k2, 0u);
+                    const uint32_t z = x | (x >> 4);
+                    const uint32_t bad = (__byte_perm(lut_lo, lut_hi, __byte_perm(z, 0, 0x0020)) ^ w[k]) & 0xDFDFDFDFu;
+                    err |= bad;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t a = lds_u32(mad_lo(e, k16, __byte_perm(v, one_addr, 0x7650u | (uint32_t)j)));
+                        e = (bad & (0xFFu << (8 * j))) ? reset_e : a;
+                        rc = mad_hi(e, k2, rc);
+                    }
+                }
+                if (POS && rc) { row0rec |= t == 0; record_hit_row(stash, nrec, t | (err ? 0u : kRowAllBases), qs, cnt); }
+                cnt += rc;
+                q = e & 0x7FFFFFFFu;
+                done = true;
+            }
+            if (!done) {
+                q = (MODE != MODE_ONE_SMEM && full) ? row_bytes_reg(T, qs, w, cnt)
+                         : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
+                                            row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
+                if (POS && cnt != before) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, before); }
+            }
         }
     }
     cp_async_wait<0>();
