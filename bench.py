@@ -457,7 +457,8 @@ def bench_plain_configs(dna, torch, stream, peak):
     out["nonconverging_256MiB_perm8"] = {
         "bytes": int(full.size), "ms_per_step": ms, "gbs": full.size / (ms * 1e-3) / 1e9,
         "matches": int(cnt.item()), "chunk_maps": bool(dfa.info().chunk_maps), "output": "count",
-        "note": "runs from different states never meet: every chunk is run from all 8 states"}
+        "note": "runs from different states never meet: every chunk is run from all 8 states, "
+                "as 4 parts walked side by side"}
     del d, full
     seq, kmers = synth.plain_large()
     dfa = dna.Dfa.from_kmers(kmers)

@@ -6,11 +6,13 @@
 // chunk and every join cascades, serially. For those the scan follows the paper's
 // possible-starting-state approach in full (Sec. III-A): a chunk is run from every state
 // at once. With at most 32 states a warp owns a chunk and lane q carries start state q;
-// all lanes read the same bytes. Each chunk yields a map (end state and count per start
-// state) and the state at each of its 32 sub-chunk boundaries per start. A single-block
-// join composes the maps in order (chunk c starts in the end state of chunk c-1 from its
-// true start), which gives the total count and every sub-chunk's exact start state. The
-// positions come from the single-sequence kernels run with those exact starts.
+// automata of at most 8 or 16 states cut the chunk into 4 or 2 parts walked side by side
+// by lane groups, and the warp composes the parts' maps. Each chunk yields a map (end
+// state and count per start state) and the state at each of its 32 sub-chunk boundaries.
+// A single-block join composes the maps in order (chunk c starts in the end state of
+// chunk c-1 from its true start), which gives the total count and every sub-chunk's exact
+// start state. The positions come from the single-sequence kernels run with those exact
+// starts.
 
 #include <cuda_runtime.h>
 
@@ -36,29 +38,37 @@ struct MapParams {
     uint64_t lo, hi;
     uint64_t chunk_bytes;       // multiple of kMapSubs * kTile
     uint32_t n_chunks;
-    uint32_t n_states;          // <= 32
+    uint32_t n_states;          // <= 32 / G for a kernel with G parts per chunk
     uint32_t reset_entry;
     const uint32_t *one;        // [n_states][4] next | accept << 31, code order A, C, T, G
     const uint32_t *pair;       // [n_states][16] compact pair entries next | count << 24
     uint32_t *map_end;          // [n_chunks][32] end state per start state
     uint32_t *map_cnt;          // [n_chunks][32] accepting steps per start state
-    uint32_t *bound;            // [n_chunks][32 sub-chunks][32 start states]
+    uint32_t *bound;            // [n_chunks][32 sub-chunks][32]: state at each sub-chunk start,
+                                //   per state at the start of the part holding that sub-chunk
+    uint32_t *gstart;           // [n_chunks][G][32]: state at the start of part g per chunk start state
     uint32_t k1, k5, lut_lo, lut_hi;
 };
 
-// One warp per chunk; lane q runs the chunk from state q (lanes at or past n_states run
-// from state 0 and are ignored). The chunk's bytes are staged 512 at a time and read by
-// every lane from the same shared address.
+// One warp per chunk. The chunk is cut into G equal parts (32 / G lanes each) walked at
+// once: lane (g, q) runs part g from state q (lanes at or past n_states run from state 0
+// and are ignored), so that small automata keep every lane busy. Each part's bytes are
+// staged 512 at a time; lane k decodes word k of every part's row for the warp. At the
+// end the warp composes the parts' maps into the chunk's map.
+template <int G>
 __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
+    constexpr uint32_t kLanes = 32u / G;               // lanes (start states) per part
+    constexpr uint32_t kWarpStage = 2u * G * kMapTile; // double-buffered tile of every part
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const uint32_t g = (uint32_t)lane / kLanes, q = (uint32_t)lane % kLanes;
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
-    // shared memory: [stages: warps x 2 x 512 B][one-symbol table: 32 x 16 B][pad][pair table]
-    uint8_t *stage = smem + (size_t)warp * 2 * kMapTile;
-    const uint32_t stage_addr = smem_base + (uint32_t)warp * 2 * kMapTile;
-    uint32_t *one_s = reinterpret_cast<uint32_t *>(smem + (size_t)kMapWarps * 2 * kMapTile);
-    const uint32_t pair_base = (smem_base + kMapWarps * 2 * kMapTile + 32 * 16 + 2047u) & ~2047u;
+    // shared memory: [stages: warps x 2 x G x 512 B][one-symbol table: 32 x 16 B][pad][pair table]
+    uint8_t *stage = smem + (size_t)warp * kWarpStage;
+    const uint32_t stage_addr = smem_base + (uint32_t)warp * kWarpStage;
+    uint32_t *one_s = reinterpret_cast<uint32_t *>(smem + (size_t)kMapWarps * kWarpStage);
+    const uint32_t pair_base = (smem_base + kMapWarps * kWarpStage + 32 * 16 + 2047u) & ~2047u;
     uint32_t *pair_s = reinterpret_cast<uint32_t *>(smem + (pair_base - smem_base));
     for (uint32_t i = threadIdx.x; i < p.n_states * 4u; i += kMapWarps * 32) one_s[i] = p.one[i];
     for (uint32_t i = threadIdx.x; i < p.n_states * 16u * 32u; i += kMapWarps * 32) {
@@ -69,24 +79,33 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
     __syncthreads();
     const uint32_t c = blockIdx.x * kMapWarps + warp;
     if (c >= p.n_chunks) return;   // warp-uniform; no barrier follows
-    __shared__ __align__(16) uint32_t ys_all[kMapWarps][32];
-    uint32_t *ys = ys_all[warp];
+    // decoded pair codes of the current row of every part (rows 36 words apart, so that
+    // parts read by the same instruction sit in different banks)
+    __shared__ __align__(16) uint32_t ys_all[kMapWarps][G][36];
+    uint32_t *ys = ys_all[warp][g];
 
     OneTable T;
     T.t = one_s;
     T.reset_entry = p.reset_entry;
     const uint64_t b = (uint64_t)c * p.chunk_bytes;
-    const uint64_t from = b > p.lo ? b : p.lo;
-    const uint64_t to = b + p.chunk_bytes < p.hi ? b + p.chunk_bytes : p.hi;
+    const uint64_t part = p.chunk_bytes / G;           // multiple of kMapTile
+    const uint64_t pb = b + g * part;                  // this lane's part
+    const uint64_t from = pb > p.lo ? pb : p.lo;
+    const uint64_t pe = pb + part < p.hi ? pb + part : p.hi;
+    const uint64_t to = pe > from ? pe : from;         // empty past the sequence end
     const uint64_t sub = p.chunk_bytes / kMapSubs;
-    const uint32_t ntiles = (uint32_t)((to - b + kMapTile - 1) / kMapTile);
-    const uint32_t q0 = (uint32_t)lane < p.n_states ? (uint32_t)lane : 0u;
+    const uint32_t ntiles = (uint32_t)(part / kMapTile);   // the same for every part and warp
+    const uint32_t q0 = q < p.n_states ? q : 0u;
     uint32_t cur = pair_base + q0 * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
     uint32_t cnt = 0;
-    auto issue = [&](uint32_t t) {   // lane copies 16 bytes of tile t (granules past hi zero-filled)
-        const uint64_t g = b + (uint64_t)t * kMapTile + (uint64_t)lane * 16u;
-        const bool ok = g < p.hi;
-        cp_async16(stage_addr + (t & 1u) * kMapTile + (uint32_t)lane * 16u, ok ? p.abase + g : p.abase, ok ? 16u : 0u);
+    auto issue = [&](uint32_t t) {   // lane copies 16 bytes of tile t of every part (past hi: zero-filled)
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+            const uint64_t off = b + (uint64_t)gg * part + (uint64_t)t * kMapTile + (uint64_t)lane * 16u;
+            const bool ok = off < p.hi;
+            cp_async16(stage_addr + ((t & 1u) * G + (uint32_t)gg) * kMapTile + (uint32_t)lane * 16u,
+                       ok ? p.abase + off : p.abase, ok ? 16u : 0u);
+        }
     };
     issue(0);
     cp_async_commit();
@@ -95,76 +114,87 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
-        const uint8_t *tile = stage + (t & 1u) * kMapTile;
+        const uint8_t *tiles = stage + (t & 1u) * G * kMapTile;
 #pragma unroll 1
         for (int r = 0; r < kMapTile / kTile; ++r) {
-            const uint64_t ro = b + (uint64_t)t * kMapTile + (uint64_t)r * kTile;
-            if (ro >= to) break;
-            if ((ro - b) % sub == 0)   // a sub-chunk starts here: record every lane's state
-                p.bound[((uint64_t)c * kMapSubs + (ro - b) / sub) * 32u + lane] =
+            const uint64_t ro = pb + (uint64_t)t * kMapTile + (uint64_t)r * kTile;
+            if (ro < to && (ro - b) % sub == 0)   // a sub-chunk starts here: record the state
+                p.bound[((uint64_t)c * kMapSubs + (ro - b) / sub) * 32u + q] =
                     ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-            const uint8_t *row = tile + r * kTile;
-            const bool full = ro >= from && ro + kTile <= to;
-            bool done = false;
-            if (full) {
-                // lane k decodes word k once for the whole warp: its pair codes (y, read
-                // back by every lane) and the base check (voted)
-                const uint32_t wk = *reinterpret_cast<const uint32_t *>(row + 4 * lane);
+            const uint8_t *row = tiles + g * kMapTile + r * kTile;
+            // lane k decodes word k of each part's row for the warp: its pair codes (y,
+            // read back by the part's lanes) and the base check (voted per part)
+            uint32_t bad_parts = 0;
+#pragma unroll
+            for (int gg = 0; gg < G; ++gg) {
+                const uint32_t wk = *reinterpret_cast<const uint32_t *>(tiles + gg * kMapTile + r * kTile + 4 * lane);
                 const uint32_t xk = wk & 0x06060606u;
-                ys[lane] = mad_lo(xk, 65u, 0u);
+                ys_all[warp][gg][lane] = mad_lo(xk, 65u, 0u);
                 const uint32_t zk = xk | (xk >> 4);
                 const bool bad = ((__byte_perm(p.lut_lo, p.lut_hi, __byte_perm(zk, 0, 0x0020)) ^ wk) & 0xDFDFDFDFu) != 0;
-                const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
-                __syncwarp();
-                if (!any_bad) {
-                    uint32_t acc = 0, rc = 0, c2 = cur;
+                bad_parts |= (__any_sync(0xFFFFFFFFu, bad) ? 1u : 0u) << gg;
+            }
+            __syncwarp();
+            const bool full = ro >= from && ro + kTile <= to;
+            if (full && !((bad_parts >> g) & 1u)) {
+                uint32_t acc = 0, rc = 0, c2 = cur;
 #pragma unroll
-                    for (int k4 = 0; k4 < 8; ++k4) {
-                        const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
-                        const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+                for (int k4 = 0; k4 < 8; ++k4) {
+                    const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
+                    const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int k = 4 * k4 + i;
-                            const uint32_t e1 = lds_u32(mux_pair(c2, yv[i]));
-                            const uint32_t e2 = lds_u32(mux_pair(e1, yv[i] >> 16));
-                            acc = mad_lo(e1, p.k1, acc);
-                            acc = mad_lo(e2, p.k1, acc);
-                            c2 = e2;
-                            if (k % 3 == 2 || k == 31) {
-                                rc = mad_hi(acc, p.k5, rc);
-                                acc = 0;
-                            }
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = 4 * k4 + i;
+                        const uint32_t e1 = lds_u32(mux_pair(c2, yv[i]));
+                        const uint32_t e2 = lds_u32(mux_pair(e1, yv[i] >> 16));
+                        acc = mad_lo(e1, p.k1, acc);
+                        acc = mad_lo(e2, p.k1, acc);
+                        c2 = e2;
+                        if (k % 3 == 2 || k == 31) {
+                            rc = mad_hi(acc, p.k5, rc);
+                            acc = 0;
                         }
                     }
-                    cnt += rc;
-                    cur = c2 & 0x3FFFFu;
-                    done = true;
                 }
-                __syncwarp();   // ys is rewritten by the next row
-            }
-            if (!done) {
+                cnt += rc;
+                cur = c2 & 0x3FFFFu;
+            } else if (ro + kTile > from && ro < to) {
                 // reset bytes or a sequence edge in this row: byte by byte
-                uint32_t q = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+                uint32_t qs = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
                 const uint32_t k0 = ro < from ? (uint32_t)(from - ro) : 0u;
                 const uint32_t k1 = ro + kTile > to ? (uint32_t)(to - ro) : (uint32_t)kTile;
                 for (uint32_t k = k0; k < k1; ++k) {
-                    const uint32_t e = T.step(q, row[k]);
-                    q = e & 0x7FFFFFFFu;
+                    const uint32_t e = T.step(qs, row[k]);
+                    qs = e & 0x7FFFFFFFu;
                     cnt += e >> 31;
                 }
-                cur = pair_base + q * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
+                cur = pair_base + qs * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u;
             }
+            __syncwarp();   // ys is rewritten by the next row
         }
         __syncwarp();   // every lane is done with this stage before it is refilled
     }
     cp_async_wait<0>();
-    p.map_end[(uint64_t)c * 32u + lane] = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
-    p.map_cnt[(uint64_t)c * 32u + lane] = cnt;
+    // compose the parts: from chunk start state s, part g starts where part g-1 ended
+    const uint32_t end = ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
+    uint32_t s = q0, total = 0;
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        if (gg > 0 && g == 0) p.gstart[((uint64_t)c * G + gg) * 32u + q] = s;
+        total += __shfl_sync(0xFFFFFFFFu, cnt, gg * (int)kLanes + (int)s);
+        s = __shfl_sync(0xFFFFFFFFu, end, gg * (int)kLanes + (int)s);
+    }
+    if (g == 0) {
+        p.map_end[(uint64_t)c * 32u + q] = s;
+        p.map_cnt[(uint64_t)c * 32u + q] = total;
+    }
 }
 
 struct JoinParams {
-    const uint32_t *map_end, *map_cnt, *bound;
+    const uint32_t *map_end, *map_cnt, *bound, *gstart;
     uint32_t n_chunks;
+    uint32_t n_states;
+    uint32_t parts;             // G of the map kernel: parts per chunk
     uint32_t *given;            // [n_chunks * 32] exact start of each sub-chunk, or null
     uint64_t *out_count;
 };
@@ -195,7 +225,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
     };
     for (uint32_t g = warp; g < ng; g += kJoinWarps) {
         const uint32_t nk = load_group(g);
-        uint32_t s = (uint32_t)lane, cc = 0;
+        uint32_t s = (uint32_t)lane < p.n_states ? (uint32_t)lane : 0u, cc = 0;
         for (uint32_t k = 0; k < nk; ++k) {
             cc += my_cnt[k * 32 + s];
             s = my_end[k * 32 + s];
@@ -220,9 +250,13 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
     for (uint32_t g = warp; g < ng; g += kJoinWarps) {
         const uint32_t nk = load_group(g);
         uint32_t s = g_start[g];
+        // sub-chunk 'lane' lies in part gl of its chunk; its recorded states are indexed
+        // by the state at that part's start
+        const uint32_t gl = (uint32_t)lane / (kMapSubs / p.parts);
         for (uint32_t k = 0; k < nk; ++k) {
             const uint64_t c = (uint64_t)g * 32 + k;
-            p.given[c * kMapSubs + lane] = p.bound[(c * kMapSubs + lane) * 32u + s];
+            const uint32_t sp = gl ? p.gstart[(c * p.parts + gl) * 32u + s] : s;
+            p.given[c * kMapSubs + lane] = p.bound[(c * kMapSubs + lane) * 32u + sp];
             s = my_end[k * 32 + s];
         }
         __syncwarp();
@@ -234,7 +268,8 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
 namespace dnalib {
 
 // The chunk-map scan of one sequence (count, and positions through scan_impl with the
-// exact sub-chunk starts). Requires n_states <= 32.
+// exact sub-chunk starts). Requires n_states <= 32. Automata of at most 8 (16) states
+// walk each chunk as 4 (2) parts at once.
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream, uint64_t *out_count,
                   uint64_t *out_positions, uint64_t cap) {
     if (d->n_states > 32 || !d->d_pair) return DNA_ERR_INVALID_ARG;
@@ -244,6 +279,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     const DeviceProps pr = device_props(d->device);
     const uint64_t warps = (uint64_t)(pr.sms ? pr.sms : 152) * kMapWarps;   // one wave of chunk warps
     const uint64_t unit = (uint64_t)kMapSubs * kTile;                        // 4 KiB
+    const uint32_t parts = d->n_states <= 8 ? 4u : d->n_states <= 16 ? 2u : 1u;
     uint64_t S = (total + warps - 1) / warps;
     S = (S + unit - 1) / unit * unit;
     const uint32_t n_chunks = (uint32_t)((total + S - 1) / S);
@@ -252,6 +288,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     const size_t o_end = take(n32 * 4), o_cnt = take(n32 * 4), o_bound = take(n32 * kMapSubs * 4);
+    const size_t o_gstart = take(n32 * parts * 4);
     const size_t o_given = positions ? take(n32 * 4) : 0;
     void *mem = nullptr;
     DNA_CUDA(cudaMallocAsync(&mem, off, stream));
@@ -262,20 +299,25 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     mp.n_states = d->n_states; mp.reset_entry = d->reset_entry; mp.one = d->d_one; mp.pair = d->d_pair;
     mp.map_end = (uint32_t *)(base + o_end); mp.map_cnt = (uint32_t *)(base + o_cnt);
     mp.bound = (uint32_t *)(base + o_bound);
+    mp.gstart = (uint32_t *)(base + o_gstart);
     mp.k1 = 1u; mp.k5 = 32u; mp.lut_lo = 0x00630061u; mp.lut_hi = 0x00670074u;
-    const size_t msmem = (size_t)kMapWarps * 2 * kMapTile + 32 * 16 + 2048 + (size_t)d->n_states * kPairRowBytes;
+    const size_t msmem = (size_t)kMapWarps * 2 * parts * kMapTile + 32 * 16 + 2048 +
+                         (size_t)d->n_states * kPairRowBytes;
     const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
-    int rc = ensure_smem_optin((const void *)map_kernel, d->device, optin - 4096);   // static: about 3 KB
+    void (*fn)(MapParams) = parts == 4 ? map_kernel<4> : parts == 2 ? map_kernel<2> : map_kernel<1>;
+    // static shared memory: the decoded rows, about 3.5 KB per part
+    int rc = ensure_smem_optin((const void *)fn, d->device, optin - 16384);
     cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
     if (e == cudaSuccess) {
         const ProfToken tk = prof_begin(stream);
-        map_kernel<<<(n_chunks + kMapWarps - 1) / kMapWarps, kMapWarps * 32, msmem, stream>>>(mp);
+        fn<<<(n_chunks + kMapWarps - 1) / kMapWarps, kMapWarps * 32, msmem, stream>>>(mp);
         e = cudaGetLastError();
         prof_end(tk, stream, PROF_SCAN);
         record_launch();
     }
     JoinParams jp;
-    jp.map_end = mp.map_end; jp.map_cnt = mp.map_cnt; jp.bound = mp.bound; jp.n_chunks = n_chunks;
+    jp.map_end = mp.map_end; jp.map_cnt = mp.map_cnt; jp.bound = mp.bound; jp.gstart = mp.gstart;
+    jp.n_chunks = n_chunks; jp.n_states = d->n_states; jp.parts = parts;
     jp.given = positions ? (uint32_t *)(base + o_given) : nullptr;
     jp.out_count = out_count;
     const uint32_t ng = (n_chunks + 31) / 32;

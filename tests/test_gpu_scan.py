@@ -222,7 +222,7 @@ def _permutation_automaton(Q, seed):
     return table, acc
 
 
-@pytest.mark.parametrize("Q", [2, 5, 17, 32])
+@pytest.mark.parametrize("Q", [2, 5, 8, 12, 17, 32])
 @pytest.mark.parametrize("n,offset", [(1, 0), (4095, 3), (100003, 7), (3 * MiB + 777, 1)])
 def test_chunk_maps_for_automata_that_never_converge(Q, n, offset):
     """Permutation automata: runs from different states never meet, so dfa_load picks
