@@ -458,7 +458,8 @@ scan_kernel(ScanParams p) {
     // run-time 2 and 16 (from k1 and k5), so the multiplies by them stay multiplies
     const uint32_t k2 = p.k1 << 1, k16 = p.k5 >> 1;
     // shared address of the one-symbol table; when it is 256-aligned its low byte is free
-    // for a code's column offset (otherwise every row is walked by row_bytes_reg)
+    // for a code's column offset (otherwise every row is walked byte by byte from global
+    // memory)
     const uint32_t one_addr = smem_base + (uint32_t)WARPS * kStages * kStageBytes;
     const bool one_fast = (one_addr & 0xFFu) == 0;
     const uint32_t reset_e = p.reset_entry;

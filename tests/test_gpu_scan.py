@@ -156,6 +156,24 @@ def test_all_reset_bytes_and_all_byte_values():
     check("regex", "TATA", lower)
 
 
+@pytest.mark.parametrize("placement", [2, 3])
+def test_one_symbol_rows_with_every_byte_value(placement):
+    """The one-symbol loops take a reset byte's entry without branching: every byte value
+    (bases of both cases, N, IUPAC codes, control and high bytes) mixed into rows of
+    bases, rows of N only and rows of lowercase bases, counts and positions."""
+    rng = np.random.default_rng(41)
+    seq = rng.integers(0, 256, size=1 * MiB + 37).astype(np.uint8)
+    bases = np.frombuffer(b"ACGTacgt", np.uint8)
+    pick = rng.random(seq.size) < 0.97
+    seq[pick] = bases[rng.integers(0, 8, size=int(pick.sum()))]
+    seq[200000:260000] = ord("N")
+    seq[300000:400000] = np.frombuffer(b"acgt", np.uint8)[rng.integers(0, 4, size=100000)]
+    for kind, pat in (("regex", "A[CG]T"), ("kmers", synth.random_kmers(41, 200, 6, 9))):
+        for chunk in (128, 2048):
+            check(kind, pat, seq, offset=3, plan=dict(chunk_bytes=chunk, placement=placement))
+    check("regex", "TATA", np.full(70000, ord("N"), np.uint8), plan=dict(placement=placement))
+
+
 def test_accepting_start_state_raw_table():
     """Raw table with state 0 in F: every reset byte is reported."""
     table = np.array([[1, 0, 0, 0], [1, 1, 0, 0]], dtype=np.uint32)
