@@ -172,3 +172,48 @@ def test_fasta_parse_capacity_and_sizing():
     big = (ctypes.c_uint8 * 8)()
     assert lib.dna_fasta_parse(text, len(text), big, 8, ctypes.byref(n_out), off2, None, 2,
                                ctypes.byref(n_rec)) == -3
+
+
+def test_argument_errors_are_reported_before_any_device_work():
+    """Invalid arguments return DNA_ERR_INVALID_ARG synchronously, from checks that run
+    before any CUDA call, so they hold with or without a GPU: an entry that names no
+    state, zero or too many states, null pointers, an empty batch or request loop."""
+    L = dna.lib()
+    p = ctypes.c_void_p
+    out = p()
+    good = np.array([[0, 1, 0, 0], [0, 1, 0, 0]], np.uint32)   # next state = f(symbol)
+    bad = good.copy()
+    bad[1, 2] = 2                      # names state 2 of a 2-state table
+    acc = np.array([2], np.uint8)
+    cases = [
+        L.dfa_load(bad.ctypes.data, 2, acc.ctypes.data, ctypes.byref(out)),
+        L.dfa_load(good.ctypes.data, 0, acc.ctypes.data, ctypes.byref(out)),
+        L.dfa_load(good.ctypes.data, (1 << 24) + 1, acc.ctypes.data, ctypes.byref(out)),
+        L.dfa_load(None, 2, acc.ctypes.data, ctypes.byref(out)),
+        L.dfa_load(good.ctypes.data, 2, None, ctypes.byref(out)),
+        L.dfa_load(good.ctypes.data, 2, acc.ctypes.data, None),
+    ]
+    depth = ctypes.c_int32()
+    cases += [
+        L.dfa_analyze(bad.ctypes.data, 2, ctypes.byref(depth)),
+        L.dfa_analyze(good.ctypes.data, 0, ctypes.byref(depth)),
+        L.dfa_info(None, None),
+    ]
+    cnt = np.zeros(1, np.uint64)
+    seq = np.frombuffer(b"ACGT", np.uint8)
+    cases += [
+        L.dna_scan(None, seq.ctypes.data, 4, None, cnt.ctypes.data, None, 0),
+        L.dna_scan_host(None, seq.ctypes.data, 4, None, cnt.ctypes.data, None, 0),
+        L.dna_scan_count_static(None, seq.ctypes.data, 4, None, cnt.ctypes.data),
+        L.dna_batch_create(None, 1, None, None, 1, None, None, ctypes.byref(out)),
+        L.dna_scan_batch(None, 0, None, None, 0, None, None),
+        L.dna_server_create(None, 1, None, ctypes.byref(out)),
+    ]
+    DNA_ERR_INVALID_ARG = -1   # include/dna_dfa.h
+    assert cases == [DNA_ERR_INVALID_ARG] * len(cases)
+    assert not out.value
+    # the analysis itself needs no device: every symbol sends both states to one state,
+    # so the table is 1-definite; with A as the identity it is not definite at all
+    assert L.dfa_analyze(good.ctypes.data, 2, ctypes.byref(depth)) == 0 and depth.value == 1
+    ident = np.array([[0, 1, 0, 0], [1, 1, 0, 0]], np.uint32)
+    assert L.dfa_analyze(ident.ctypes.data, 2, ctypes.byref(depth)) == 0 and depth.value == -1
