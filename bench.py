@@ -147,6 +147,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+def host_cpu() -> dict:
+    """The host's logical CPU count and CPU model (lscpu 'Model name', else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
 def cpu_oracle_rate(seq: np.ndarray, pattern: str, seconds: float):
     """The oracle (single-threaded C) on consecutive 32 MiB slices of the workload until
     'seconds' have elapsed; returns (GB/s, bytes scanned)."""
@@ -191,7 +213,7 @@ def run_reference(args, rank, world):
         "data": "synthetic", "config": {"workload": WORKLOAD, "bytes_per_step": n,
                                         "sample": f"first {n} bytes of the workload per step"},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n} bytes of the 256 MiB sequence per step"},
+                         "sample": f"first {n} bytes of the 256 MiB sequence per step", **host_cpu()},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -205,6 +227,37 @@ def lds_lookup_peak(sms: int, mhz: float) -> float:
     """Shared-memory lookups per second the SMs can issue: one 32-lane LDS wavefront per
     SM per clock (bank-conflict free)."""
     return sms * 32 * mhz * 1e6
+
+
+def cpu_batched_rate(buf, offs, regexes, seconds: float):
+    """The oracle (unchanged, single-threaded C) over independent (sequence, automaton)
+    pairs of the batched workload, one pair per task on every host core (ctypes releases
+    the GIL during each run). Sequences are taken in a seeded random order, each against
+    all automata, until 'seconds' have elapsed. Returns the (sequence x automaton) GB/s,
+    the threads used and the sample."""
+    import concurrent.futures as cf
+    import oracle
+    tables = [oracle.compile_regex(r) for r in regexes]
+    order = np.random.Generator(np.random.PCG64(3)).permutation(offs.size - 1)
+    threads = os.cpu_count() or 1
+    done_bytes, pairs, seqs = 0, 0, 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        for si in order:
+            part = buf[int(offs[si]):int(offs[si + 1])]
+            futs = [ex.submit(oracle.run, t, a, part, False) for t, a in tables]
+            for f in futs:
+                f.result()
+            done_bytes += part.size * len(tables)
+            pairs += len(tables)
+            seqs += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+    el = time.perf_counter() - t0
+    return {"value": done_bytes / el / 1e9, "unit": "GB/s (sequence x automaton)", "cores": threads,
+            "kind": "oracle", "sample": f"{seqs} sequences x {len(tables)} automata ({pairs} pairs, "
+                                        f"{done_bytes / 1e9:.2f} GB of sequence x automaton) in a seeded random "
+                                        f"order, one pair per task on {threads} threads", **host_cpu()}
 
 
 def bench_batched(args, dna, torch, stream, clocks_mhz):
@@ -223,7 +276,11 @@ def bench_batched(args, dna, torch, stream, clocks_mhz):
         dbuf[pos:pos + lens[i]].copy_(hbuf[int(offs[i]):int(offs[i + 1])])
         starts.append(dbuf.data_ptr() + pos)
         pos += (lens[i] + 255) // 256 * 256
-    del hbuf, buf
+    del hbuf
+    cpu_batched = None
+    if not args.no_cpu_baseline:
+        cpu_batched = cpu_batched_rate(buf, offs, regexes, args.cpu_seconds)
+    del buf
     dfas = [dna.Dfa.from_regex(r) for r in regexes]
     states = [d.info().n_states for d in dfas]
     t0 = time.perf_counter()
@@ -272,6 +329,7 @@ def bench_batched(args, dna, torch, stream, clocks_mhz):
         "seq_x_dfa_gbs": total * len(dfas) / (ms * 1e-3) / 1e9,
         "ingest_ms": i_ms, "batch_kernel_ms": k_ms,
         "total_matches": int(counts.sum()),
+        "cpu_baseline": cpu_batched,
     }
     peak = lds_lookup_peak(torch.cuda.get_device_properties(0).multi_processor_count, clocks_mhz or 2070.0)
     lookups = total * info.n_fast * 0.5    # one two-symbol lookup per 2 bases per automaton
@@ -537,6 +595,23 @@ def main():
     ms_step = ms_total / args.steps
     value = n * world / (ms_step * 1e-3) / 1e9
 
+    # ---- where a short run's time goes: the same number of steps (at most 50) after the
+    # same idle pause, with an event pair around every step
+    n_diag = max(1, min(args.steps, 50))
+    torch.cuda.synchronize()
+    time.sleep(0.3)
+    dev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_diag)]
+    for a, b in dev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    per_step_us = [a.elapsed_time(b) * 1e3 for a, b in dev]
+    step_times = {"steps": n_diag, "first_us": per_step_us[0],
+                  "median_us": statistics.median(per_step_us),
+                  "max_us": max(per_step_us), "min_us": min(per_step_us),
+                  "note": "device time of each step (events around it) after a 0.3 s idle pause"}
+
     # ---- the scan kernel's own time: a separate pass with per-launch events (the timed
     # region above runs without them)
     prof_steps = max(1, min(args.steps, 2000))
@@ -546,6 +621,9 @@ def main():
     torch.cuda.synchronize()
     dna.profile_enable(False)
     prof = dna.profile_read(reset=True)
+    emit_ms = prof["emit_kernel_ms"] / max(1, prof["emit_kernel_calls"])
+    step_times["scan_kernel_us"] = prof["scan_kernel_ms"] / max(1, prof["scan_kernel_calls"]) * 1e3
+    step_times["emit_kernel_us"] = emit_ms * 1e3
     ns = max(1, prof["conv_scans"])
     chunks = prof["conv_chunks"] / ns
     speculation = {
@@ -612,7 +690,7 @@ def main():
         rate, done = cpu_oracle_rate(seq_np, pattern, args.cpu_seconds)
         cpu = {"value": rate, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{done / MiB:.0f} MiB scanned as 32 MiB slices of the 256 MiB workload "
-                         f"(count + positions), single thread"}
+                         f"(count + positions), single thread", **host_cpu()}
 
     plain_configs = None
     if world == 1 and not args.no_plain_configs:
@@ -641,6 +719,7 @@ def main():
                        "e2e_steps": e2e_steps},
             "roofline": roofline,
             "speculation": speculation,
+            "step_times": step_times,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": n,
                     "d2h_bytes_per_step": 8 + 8 * n_matches, "ms_per_step": e2e_ms,

@@ -125,10 +125,15 @@ int dfa_analyze(const uint32_t *table, uint32_t n_states, int32_t *definite_dept
  *                  min(count, positions_capacity) match positions (uint64, ascending).
  *                  A count above positions_capacity is visible as *out_count >
  *                  positions_capacity; the written positions are then the smallest
- *                  positions_capacity ones.
+ *                  positions_capacity ones. (The call returns before the count exists
+ *                  on the device, so it cannot return DNA_ERR_CAPACITY for this; the
+ *                  synchronous dna_scan_host does.)
  *   positions_capacity  number of uint64 slots at out_positions.
- * Scratch: the call allocates stream-ordered device scratch (cudaMallocAsync) sized
- * O(len / chunk) and frees it on the same stream.
+ * Scratch: the call takes stream-ordered device scratch sized O(len / chunk) from a
+ * memory pool the library keeps per device, and returns it on the same stream. The pool
+ * keeps up to 1 GiB reserved between calls, so repeated calls map no new memory.
+ * No kernel of a scan waits on another block or on the host, so no device-side error
+ * can arise after the call returns except CUDA's own (reported by the stream).
  * Kernels: one chunk-scan kernel (speculation, chunk scan, join) and, with positions,
  * one extraction kernel; automata using chunk maps run a map kernel and a join kernel
  * first (and, with positions, the chunk-scan kernels from the exact chunk starts).
@@ -167,13 +172,17 @@ int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64_t len, dna
  *   Limits: len <= 2^36 bytes (64 GiB); a length or automaton whose chunk bookkeeping
  *   would not fit in the 4 MiB array returns DNA_ERR_CAPACITY before any work is queued.
  *   Set-up: the first call on a device looks up the array's device address (with that
- *   device current); make that first call before any stream capture.
+ *   device current) and keeps it for the life of the process; make that first call
+ *   before any stream capture, and do not call this entry point again after a reset of
+ *   the device (cudaDeviceReset), which reloads the library's device code and moves the
+ *   array.
  *   Sharing: all calls use the same array, which keeps the previous call's contents;
  *   calls that overlap on the GPU (different streams, or no ordering between them)
  *   race on it and give wrong counts. Order the calls, e.g. issue them on one stream.
- *   No cudaMalloc, cudaFree or allocating library routine is called.
- *   Automata that dna_scan runs with chunk maps are scanned here with speculation and
- *   repair (exact, but slow when runs from different states never meet).
+ *   No cudaMalloc, cudaFree or allocating library routine is called (the library's
+ *   allocation counter, dna_profile_t.device_allocs, does not move).
+ *   Automata that dna_scan runs with chunk maps (dna_dfa_info.chunk_maps) run the same
+ *   chunk-map kernels here, with their per-chunk maps in the array.
  * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_CAPACITY, DNA_ERR_CUDA.
  */
 int dna_scan_count_static(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
@@ -426,6 +435,9 @@ typedef struct {
     uint64_t conv_blockfirst;   /* first chunks of blocks joined with a wrong start */
     uint64_t conv_diverged;     /* repairs that changed a chunk's last state */
     uint64_t conv_cascade;      /* chunks re-walked by the cascade */
+    /* device allocations the library has made since it was loaded (handles, plans and
+       stream-ordered scratch; never reset): */
+    uint64_t device_allocs;
 } dna_profile_t;
 
 void dna_profile_enable(int enable);

@@ -61,7 +61,7 @@ class _Profile(ctypes.Structure):
                 ("conv_scans", ctypes.c_uint64), ("conv_chunks", ctypes.c_uint64),
                 ("conv_inblock", ctypes.c_uint64), ("conv_pending", ctypes.c_uint64),
                 ("conv_blockfirst", ctypes.c_uint64), ("conv_diverged", ctypes.c_uint64),
-                ("conv_cascade", ctypes.c_uint64)]
+                ("conv_cascade", ctypes.c_uint64), ("device_allocs", ctypes.c_uint64)]
 
 
 class _BatchOpts(ctypes.Structure):

@@ -558,7 +558,10 @@ int autotune(dna_batch &b, cudaStream_t stream) {
     const uint32_t tiles_c[] = {4, 8, 16, 32};
     const uint32_t warps_c[] = {16, 24};
     uint64_t *tmp = nullptr;
-    DNA_CUDA(cudaMallocAsync(&tmp, (size_t)b.n_seqs * b.n_dfas * 8, stream));
+    {
+        const int ra = scratch_alloc(b.device, (size_t)b.n_seqs * b.n_dfas * 8, stream, (void **)&tmp);
+        if (ra) return ra;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -584,7 +587,7 @@ int autotune(dna_batch &b, cudaStream_t stream) {
     saved_slow.swap(b.slow);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFreeAsync(tmp, stream);
+    scratch_free(tmp, stream);
     if (rc) return rc;
     return batch_plan_kernel(b, bt, bw, stream);
 }
@@ -679,7 +682,7 @@ extern "C" int dna_batch_create(const dna_dfa *const *dfas, uint32_t n_dfas, con
     const size_t o_dfas = take(descs.size() * sizeof(BatchDfa) + 8), o_chunks = take(chunk_cap * 8 + 8);
     const size_t o_ticket = take(16), o_tflags = take(tiles + 16);
     const size_t o_codes = take(b->fast.empty() ? 16 : tiles * (size_t)kTile + 16);
-    cudaError_t e = cudaMalloc(&b->mem, off);
+    cudaError_t e = device_alloc((void **)&b->mem, off);
     if (e != cudaSuccess) { release(b); return cuda_status(e); }
     b->d_seqs = reinterpret_cast<const uint8_t **>(b->mem + o_seqs);
     b->d_lens = reinterpret_cast<uint64_t *>(b->mem + o_lens);

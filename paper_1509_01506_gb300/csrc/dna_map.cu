@@ -46,7 +46,9 @@ struct MapParams {
     uint32_t *map_cnt;          // [n_chunks][32] accepting steps per start state
     uint32_t *bound;            // [n_chunks][32 sub-chunks][32]: state at each sub-chunk start,
                                 //   per state at the start of the part holding that sub-chunk
-    uint32_t *gstart;           // [n_chunks][G][32]: state at the start of part g per chunk start state
+                                //   (null for a count-only scan)
+    uint32_t *gstart;           // [n_chunks][G][32]: state at the start of part g per chunk start
+                                //   state (null for a count-only scan)
     uint32_t k1, k5, lut_lo, lut_hi;
 };
 
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
 #pragma unroll 1
         for (int r = 0; r < kMapTile / kTile; ++r) {
             const uint64_t ro = pb + (uint64_t)t * kMapTile + (uint64_t)r * kTile;
-            if (ro < to && (ro - b) % sub == 0)   // a sub-chunk starts here: record the state
+            if (p.bound && ro < to && (ro - b) % sub == 0)   // a sub-chunk starts here: record the state
                 p.bound[((uint64_t)c * kMapSubs + (ro - b) / sub) * 32u + q] =
                     ((cur & 0x3FFFFu) - pair_base) / (uint32_t)kPairRowBytes;
             const uint8_t *row = tiles + g * kMapTile + r * kTile;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
     uint32_t s = q0, total = 0;
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) {
-        if (gg > 0 && g == 0) p.gstart[((uint64_t)c * G + gg) * 32u + q] = s;
+        if (p.gstart && gg > 0 && g == 0) p.gstart[((uint64_t)c * G + gg) * 32u + q] = s;
         total += __shfl_sync(0xFFFFFFFFu, cnt, gg * (int)kLanes + (int)s);
         s = __shfl_sync(0xFFFFFFFFu, end, gg * (int)kLanes + (int)s);
     }
@@ -269,9 +271,10 @@ namespace dnalib {
 
 // The chunk-map scan of one sequence (count, and positions through scan_impl with the
 // exact sub-chunk starts). Requires n_states <= 32. Automata of at most 8 (16) states
-// walk each chunk as 4 (2) parts at once.
+// walk each chunk as 4 (2) parts at once. 'ext' (count only) supplies the scratch instead
+// of the library's pool: ext_bytes of device memory; DNA_ERR_CAPACITY when it is too small.
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream, uint64_t *out_count,
-                  uint64_t *out_positions, uint64_t cap) {
+                  uint64_t *out_positions, uint64_t cap, uint8_t *ext, size_t ext_bytes) {
     if (d->n_states > 32 || !d->d_pair) return DNA_ERR_INVALID_ARG;
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;
@@ -284,22 +287,31 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     S = (S + unit - 1) / unit * unit;
     const uint32_t n_chunks = (uint32_t)((total + S - 1) / S);
     const bool positions = out_positions != nullptr && cap > 0;
+    if (ext && positions) return DNA_ERR_INVALID_ARG;
     const size_t n32 = (size_t)n_chunks * 32;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_end = take(n32 * 4), o_cnt = take(n32 * 4), o_bound = take(n32 * kMapSubs * 4);
-    const size_t o_gstart = take(n32 * parts * 4);
+    const size_t o_end = take(n32 * 4), o_cnt = take(n32 * 4);
+    // sub-chunk states, only for the positions pass
+    const size_t o_bound = positions ? take(n32 * kMapSubs * 4) : 0;
+    const size_t o_gstart = positions ? take(n32 * parts * 4) : 0;
     const size_t o_given = positions ? take(n32 * 4) : 0;
     void *mem = nullptr;
-    DNA_CUDA(cudaMallocAsync(&mem, off, stream));
+    if (ext) {
+        if (off > ext_bytes) return DNA_ERR_CAPACITY;
+        mem = ext;
+    } else {
+        const int ra = scratch_alloc(d->device, off, stream, &mem);
+        if (ra) return ra;
+    }
     uint8_t *base = (uint8_t *)mem;
 
     MapParams mp;
     mp.abase = abase; mp.lo = shift; mp.hi = total; mp.chunk_bytes = S; mp.n_chunks = n_chunks;
     mp.n_states = d->n_states; mp.reset_entry = d->reset_entry; mp.one = d->d_one; mp.pair = d->d_pair;
     mp.map_end = (uint32_t *)(base + o_end); mp.map_cnt = (uint32_t *)(base + o_cnt);
-    mp.bound = (uint32_t *)(base + o_bound);
-    mp.gstart = (uint32_t *)(base + o_gstart);
+    mp.bound = positions ? (uint32_t *)(base + o_bound) : nullptr;
+    mp.gstart = positions ? (uint32_t *)(base + o_gstart) : nullptr;
     mp.k1 = 1u; mp.k5 = 32u; mp.lut_lo = 0x00630061u; mp.lut_hi = 0x00670074u;
     const size_t msmem = (size_t)kMapWarps * 2 * parts * kMapTile + 32 * 16 + 2048 +
                          (size_t)d->n_states * kPairRowBytes;
@@ -340,8 +352,10 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
         pl.placement = DNA_PLACE_SMEM_PAIR;
         rc = scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, &pl, jp.given);
     }
-    cudaError_t e2 = cudaFreeAsync(mem, stream);
-    if (rc == DNA_OK && e2 != cudaSuccess) rc = cuda_status(e2);
+    if (!ext) {
+        const int rf = scratch_free(mem, stream);
+        if (rc == DNA_OK) rc = rf;
+    }
     return rc;
 }
 

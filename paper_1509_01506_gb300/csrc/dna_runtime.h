@@ -46,6 +46,20 @@ size_t align_up(size_t x, size_t a);
 // Counts kernels launched by the library (reported by dna_profile_read).
 void record_launch(int n = 1);
 
+// Device memory the library allocates; every allocation is counted (dna_profile_read's
+// device_allocs).
+// scratch_alloc / scratch_free: stream-ordered scratch from the library's own memory pool
+// on device 'dev' (created on first use). The pool keeps up to kScratchKeepBytes
+// reserved between calls: the device's default pool hands its memory back at every
+// synchronisation, and the next call would then map it again.
+constexpr uint64_t kScratchKeepBytes = 1ull << 30;
+int scratch_alloc(int dev, size_t bytes, cudaStream_t s, void **out);
+int scratch_free(void *p, cudaStream_t s);
+// device_alloc: a plain (counted) cudaMalloc for memory that lives as long as a handle.
+cudaError_t device_alloc(void **p, size_t bytes);
+// pool_alloc: a (counted) stream-ordered allocation from a pool the caller owns.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t s);
+
 // The single-sequence scan behind dna_scan / dna_scan_planned (dispatches to the
 // chunk-map path for automata that need it).
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
@@ -55,9 +69,11 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
 int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                     uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
                     const uint32_t *given_start);
-// The chunk-map scan (dna_map.cu); n_states <= 32.
+// The chunk-map scan (dna_map.cu); n_states <= 32. 'ext' (count only, or null) is
+// caller-provided scratch of ext_bytes bytes used instead of the library's pool.
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
-                  uint64_t *out_count, uint64_t *out_positions, uint64_t cap);
+                  uint64_t *out_count, uint64_t *out_positions, uint64_t cap,
+                  uint8_t *ext = nullptr, size_t ext_bytes = 0);
 
 // Kernel timing: prof_begin records an event on the stream when profiling is enabled
 // (otherwise returns an empty token); prof_end records the closing event.

@@ -384,6 +384,56 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 std::atomic<uint64_t> g_launches{0};
 void record_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+static std::atomic<uint64_t> g_dev_allocs{0};
+
+cudaError_t device_alloc(void **p, size_t bytes) {
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t s) {
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// The library's scratch pools, one per device, created on first use and kept for the
+// life of the process.
+static std::mutex g_pool_mu;
+static std::vector<cudaMemPool_t> g_pools;
+
+int scratch_alloc(int dev, size_t bytes, cudaStream_t s, void **out) {
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+        if (!g_pools[dev]) {
+            cudaMemPoolProps pp = {};
+            pp.allocType = cudaMemAllocationTypePinned;
+            pp.handleTypes = cudaMemHandleTypeNone;
+            pp.location.type = cudaMemLocationTypeDevice;
+            pp.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            DNA_CUDA(cudaMemPoolCreate(&np, &pp));
+            uint64_t keep = kScratchKeepBytes;
+            cudaError_t e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(np);
+                return cuda_status(e);
+            }
+            g_pools[dev] = np;
+        }
+        pool = g_pools[dev];
+    }
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    DNA_CUDA(cudaMallocFromPoolAsync(out, bytes, pool, s));
+    return DNA_OK;
+}
+
+int scratch_free(void *p, cudaStream_t s) {
+    if (!p) return DNA_OK;
+    return cuda_status(cudaFreeAsync(p, s));
+}
+
 // Kernel timing for dna_profile_*: an event pair around each timed launch, resolved
 // (and recycled) when the counters are read.
 static std::atomic<int> g_profile{0};
@@ -486,6 +536,7 @@ void profile_collect(dna_profile_t *out, int reset) {
     out->conv_blockfirst = g_conv[4];
     out->conv_diverged = g_conv[5];
     out->conv_cascade = g_conv[6];
+    out->device_allocs = g_dev_allocs.load();
     if (reset) {
         for (int k = 0; k < PROF_N; ++k) { g_prof_ms[k] = 0; g_prof_calls[k] = 0; }
         for (int k = 0; k < 7; ++k) g_conv[k] = 0;
@@ -678,7 +729,8 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     Scratch s;
     carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, nullptr);
     void *mem = nullptr;
-    DNA_CUDA(cudaMallocAsync(&mem, s.bytes, stream));
+    rc = scratch_alloc(d->device, s.bytes, stream, &mem);
+    if (rc) return rc;
     carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, (uint8_t *)mem);
     cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 32, stream);
 
@@ -740,9 +792,9 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
             record_launch();
         }
     }
-    cudaError_t e2 = cudaFreeAsync(mem, stream);
-    if (e == cudaSuccess) e = e2;
-    return cuda_status(e);
+    const int rf = scratch_free(mem, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return rf;
 }
 
 }  // namespace dnalib
@@ -805,7 +857,7 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
     if (n_states <= max_pair_states(optin, 8)) d->placement = DNA_PLACE_SMEM_PAIR;
     else if (scan_total_smem(MODE_ONE_SMEM, 8, n_states) <= optin) d->placement = DNA_PLACE_SMEM_ONE;
     else d->placement = DNA_PLACE_GLOBAL_ONE;
-    cudaError_t e = cudaMalloc(&d->d_one, sizeof(uint32_t) * one.size());
+    cudaError_t e = device_alloc((void **)&d->d_one, sizeof(uint32_t) * one.size());
     if (e == cudaSuccess) e = cudaMemcpy(d->d_one, one.data(), sizeof(uint32_t) * one.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_states <= max_pair_states(optin, 8)) {
         std::vector<uint32_t> pair(16ull * n_states);
@@ -819,7 +871,7 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
                     uint32_t cnt = (e1 >> 31) + (e2 >> 31);
                     pair[16ull * q + b0 + 4 * b1] = q2 | (cnt << 24);
                 }
-        e = cudaMalloc(&d->d_pair, sizeof(uint32_t) * pair.size());
+        e = device_alloc((void **)&d->d_pair, sizeof(uint32_t) * pair.size());
         if (e == cudaSuccess) e = cudaMemcpy(d->d_pair, pair.data(), sizeof(uint32_t) * pair.size(), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
@@ -869,7 +921,10 @@ extern "C" int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64
     const uint64_t cap = positions_host ? positions_capacity : 0;
     const size_t seq_off = align_up(8 + (size_t)cap * 8, 256);
     void *mem = nullptr;
-    DNA_CUDA(cudaMallocAsync(&mem, seq_off + (size_t)len + 16, stream));
+    {
+        const int ra = scratch_alloc(dfa->device, seq_off + (size_t)len + 16, stream, &mem);
+        if (ra) return ra;
+    }
     uint8_t *base = (uint8_t *)mem;
     uint64_t *d_count = (uint64_t *)base;
     uint64_t *d_pos = cap ? (uint64_t *)(base + 8) : nullptr;
@@ -888,9 +943,9 @@ extern "C" int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64
             }
         }
     }
-    cudaError_t ef = cudaFreeAsync(mem, stream);
-    if (e == cudaSuccess) e = ef;
+    const int rf = scratch_free(mem, stream);
     if (rc != DNA_OK) return rc;
+    if (e == cudaSuccess && rf != DNA_OK) return rf;
     if (e != cudaSuccess) return cuda_status(e);
     return cap && *count_host > cap ? DNA_ERR_CAPACITY : DNA_OK;
 }
@@ -948,6 +1003,12 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
         write_zero_kernel<<<1, 1, 0, stream>>>(out_count);
         record_launch();
         return cuda_status(cudaGetLastError());
+    }
+    if (d->map_mode) {
+        // automata whose runs never meet: the chunk-map kernels, as dna_scan runs them,
+        // with their per-chunk maps in the fixed array
+        return map_scan_impl(d, seq, len, stream, out_count, nullptr, 0, (uint8_t *)base,
+                             kStaticScratchBytes);
     }
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;

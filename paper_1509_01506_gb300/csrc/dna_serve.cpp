@@ -94,7 +94,7 @@ int admit(dna_server &s, Slot &sl, const Request &r) {
     sl.status = DNA_OK;
     cudaError_t e = cudaEventRecord(sl.ev_start, sl.stream);
     if (e == cudaSuccess && r.len)
-        e = cudaMallocFromPoolAsync(&sl.d_seq, r.len + 16, s.pool, sl.stream);
+        e = pool_alloc(&sl.d_seq, r.len + 16, s.pool, sl.stream);
     if (e == cudaSuccess && r.len)
         e = cudaMemcpyAsync(sl.d_seq, r.host, r.len, cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev_h2d, sl.stream);
@@ -252,7 +252,7 @@ extern "C" int dna_server_create(const dna_dfa *const *dfas, uint32_t n_dfas, co
         if (e == cudaSuccess) e = cudaEventCreate(&sl.ev_start);
         if (e == cudaSuccess) e = cudaEventCreate(&sl.ev_h2d);
         if (e == cudaSuccess) e = cudaEventCreate(&sl.ev_end);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_count, 8);
+        if (e == cudaSuccess) e = device_alloc((void **)&sl.d_count, 8);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_count, 8);
     }
     if (e == cudaSuccess) {

@@ -138,3 +138,30 @@ def test_request_loop_with_a_chunk_map_automaton(workload):
         o, n = ids[c["id"]]
         assert c["status"] == 0
         assert c["count"] == oracle.run(table.astype(np.int32), acc, payload[o:o + n], positions=False)[0]
+
+
+def test_drain_with_a_short_limit_times_out_and_a_later_drain_completes(workload):
+    """dna_server_drain's limit: with a 40 MiB request on the device and a second one
+    not due for another 300 ms, a 1 ms drain returns DNA_ERR_TIMEOUT (the server keeps
+    running); a drain without a limit then finishes both, with the oracle's counts."""
+    pinned, _, _, _, _, dfas = workload
+    payload = pinned.numpy()
+    n = 40 * MiB
+    srv = dna.Server(dfas[:1], slots=2)
+    base = pinned.data_ptr()
+    first = srv.submit((base, n), 0)
+    second = srv.submit((base + 4096, n), 0, dna.Server.now_ns() + 300_000_000)
+    with pytest.raises(dna.DnaError) as err:
+        srv.drain(timeout_ms=1)
+    assert err.value.code == -4 and dna.status_string(-4) == "device wait timed out"
+    st = srv.stats()
+    assert st["submitted"] == 2 and st["completed"] < 2
+    srv.drain()
+    comps = {c["id"]: c for c in srv.poll(8)}
+    srv.free()
+    assert set(comps) == {first, second}
+    t, a = oracle.compile_regex(synth.random_regexes(21, 1)[0])
+    for rid, off in ((first, 0), (second, 4096)):
+        assert comps[rid]["status"] == 0
+        assert comps[rid]["count"] == oracle.run(t, a, payload[off:off + n], positions=False)[0]
+    assert comps[second]["admit_ns"] >= comps[second]["arrival_ns"]
