@@ -517,6 +517,19 @@ def bench_plain_configs(dna, torch, stream, peak):
         "matches": int(cnt.item()), "chunk_maps": bool(dfa.info().chunk_maps), "output": "count",
         "note": "runs from different states never meet: every chunk is run from all 8 states, "
                 "as 4 parts walked side by side"}
+    # 64 states whose runs never meet: two warps per chunk, one per block of 32 start states
+    rng = np.random.Generator(np.random.PCG64(64))
+    table = np.stack([rng.permutation(64) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = (rng.random(64) < 0.25).astype(np.uint8)
+    acc[0] = 0
+    acc[int(rng.integers(1, 64))] = 1
+    dfa64 = dna.Dfa(table, dna.pack_accept(acc))
+    fn = lambda: dna.scan(dfa64, d, stream=stream, out_count=cnt)
+    ms = timed(fn, 5)
+    out["nonconverging_256MiB_perm64"] = {
+        "bytes": int(full.size), "ms_per_step": ms, "gbs": full.size / (ms * 1e-3) / 1e9,
+        "matches": int(cnt.item()), "chunk_maps": bool(dfa64.info().chunk_maps), "output": "count",
+        "note": "64 states whose runs never meet: every chunk is run from all 64 states by two warps"}
     del d, full
     seq, kmers = synth.plain_large()
     dfa = dna.Dfa.from_kmers(kmers)

@@ -71,7 +71,7 @@ typedef struct dna_dfa dna_dfa; /* opaque; its tables live in device memory */
  * The table is copied (the caller may free its buffers on return). dfa_load also
  * analyses the automaton on the host (its definite depth: the smallest m such that
  * any m symbols bring every state to one state, when m <= 64; and, for automata of at
- * most 32 states that are not definite, whether runs from all states meet within 16
+ * most 256 states that are not definite, whether runs from all states meet within 16
  * symbols of random DNA) and picks the speculation lookback, the table placement and
  * whether scans use chunk maps (DNA_PLACE_MAP).
  * Errors: DNA_ERR_INVALID_ARG, DNA_ERR_NOMEM, DNA_ERR_CUDA, DNA_ERR_NO_DEVICE.
@@ -96,11 +96,13 @@ typedef struct {
 #define DNA_PLACE_SMEM_PAIR  1  /* two-symbol table, one copy per lane, shared memory */
 #define DNA_PLACE_SMEM_ONE   2  /* one-symbol table in shared memory */
 #define DNA_PLACE_GLOBAL_ONE 3  /* one-symbol table in global memory (L2 resident) */
-/* Chunk maps (automata of at most 32 states): a warp runs each chunk from every state at
- * once (the possible starting states of Sec. III-A taken in full), a join composes the
- * chunk maps in order. dfa_load picks it for automata whose runs from different states
- * do not meet within 16 symbols of random DNA (speculation would rarely be repaired in
- * the chunk's first bytes); it can also be requested through dna_plan.placement. */
+/* Chunk maps (automata of at most 256 states): each chunk is run from every state at once
+ * (the possible starting states of Sec. III-A taken in full; a warp per 32 start states),
+ * and a join composes the chunk maps in order. dfa_load picks it for automata whose runs
+ * from different states do not meet within 16 symbols of random DNA (speculation would
+ * rarely be repaired in the chunk's first bytes); it can also be requested through
+ * dna_plan.placement. Larger automata whose runs never meet are scanned with speculation
+ * and repair, which is exact but walks every chunk boundary in order. */
 #define DNA_PLACE_MAP        4
 
 int dfa_info(const dna_dfa *dfa, dna_dfa_info *out);

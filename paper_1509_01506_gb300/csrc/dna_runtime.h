@@ -69,8 +69,9 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
 int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                     uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
                     const uint32_t *given_start);
-// The chunk-map scan (dna_map.cu); n_states <= 32. 'ext' (count only, or null) is
-// caller-provided scratch of ext_bytes bytes used instead of the library's pool.
+// The chunk-map scan (dna_map.cu); n_states <= kMaxMapStates. 'ext' (count only, or
+// null) is caller-provided scratch of ext_bytes bytes used instead of the library's pool.
+constexpr uint32_t kMaxMapStates = 256;
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                   uint64_t *out_count, uint64_t *out_positions, uint64_t cap,
                   uint8_t *ext = nullptr, size_t ext_bytes = 0);

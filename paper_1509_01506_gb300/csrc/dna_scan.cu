@@ -686,7 +686,7 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
     const uint32_t req = ov ? ov->placement : 0u;
     if (req > DNA_PLACE_MAP) return DNA_ERR_INVALID_ARG;
     if (req == DNA_PLACE_MAP || (req == 0 && d->map_mode)) {
-        if (d->n_states > 32 || !d->d_pair) return DNA_ERR_CAPACITY;
+        if (d->n_states > kMaxMapStates) return DNA_ERR_CAPACITY;
         if (len > (1ull << 40)) return DNA_ERR_INVALID_ARG;
         int cur_dev = -1;
         DNA_CUDA(cudaGetDevice(&cur_dev));
@@ -832,22 +832,31 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
     d->lookback = (d->definite_depth > 16) ? (uint32_t)d->definite_depth : 0u;
     // automata that are not definite within 64 symbols: do the runs from all states meet
     // within 16 symbols of typical DNA? Checked on 8 seeded random windows of 256 bases
-    // (small automata only); if not, scans run every chunk from every state (chunk maps)
-    if (d->definite_depth < 0 && n_states <= 32) {
+    // (automata of at most kMaxMapStates states); if not, scans run every chunk from every
+    // state (chunk maps)
+    if (d->definite_depth < 0 && n_states <= kMaxMapStates) {
         uint64_t x = 0x9E3779B97F4A7C15ull;
         int slow = 0;
+        const uint32_t nw = (n_states + 63) / 64;
+        std::vector<uint64_t> live(nw), next(nw);
         for (int trial = 0; trial < 8; ++trial) {
-            uint32_t live = n_states == 32 ? 0xFFFFFFFFu : ((1u << n_states) - 1u);
+            for (uint32_t q = 0; q < n_states; ++q) live[q >> 6] |= 1ull << (q & 63);
             int met = -1;
             for (int k = 0; k < 256 && met < 0; ++k) {
                 x ^= x << 13; x ^= x >> 7; x ^= x << 17;
                 const uint32_t col = (uint32_t)(x >> 62);
-                uint32_t next = 0;
+                std::fill(next.begin(), next.end(), 0ull);
+                uint32_t n_live = 0;
                 for (uint32_t q = 0; q < n_states; ++q)
-                    if (live >> q & 1u) next |= 1u << table[q * 4u + col];
-                live = next;
-                if ((live & (live - 1u)) == 0) met = k + 1;
+                    if (live[q >> 6] >> (q & 63) & 1u) {
+                        const uint32_t t = table[q * 4u + col];
+                        next[t >> 6] |= 1ull << (t & 63);
+                    }
+                live.swap(next);
+                for (uint64_t w : live) n_live += (uint32_t)__builtin_popcountll(w);
+                if (n_live <= 1) met = k + 1;
             }
+            std::fill(live.begin(), live.end(), 0ull);
             if (met < 0 || met > 16) ++slow;
         }
         d->map_mode = slow > 2;

@@ -240,7 +240,7 @@ def _permutation_automaton(Q, seed):
     return table, acc
 
 
-@pytest.mark.parametrize("Q", [2, 5, 8, 12, 17, 32])
+@pytest.mark.parametrize("Q", [2, 5, 8, 12, 17, 32, 33, 64, 90, 91, 130, 256])
 @pytest.mark.parametrize("n,offset", [(1, 0), (4095, 3), (100003, 7), (3 * MiB + 777, 1)])
 def test_chunk_maps_for_automata_that_never_converge(Q, n, offset):
     """Permutation automata: runs from different states never meet, so dfa_load picks
@@ -255,6 +255,36 @@ def test_chunk_maps_for_automata_that_never_converge(Q, n, offset):
     assert c == want_c and np.array_equal(p, want_p)
     c2, _ = gpu_run(dfa, to_device(seq, offset), positions=False)
     assert c2 == want_c
+
+
+@pytest.mark.parametrize("Q", [33, 64, 256])
+def test_chunk_maps_of_more_than_32_states_at_64MiB(Q):
+    """Automata of more than 32 states whose runs never meet: every chunk is run from
+    every state by ceil(Q / 32) warps (two-symbol tables up to about 90 states, one-symbol
+    tables above), the wide maps are composed by the join; counts and positions of a
+    64 MiB noisy Markov sequence equal the oracle's."""
+    table, acc = _permutation_automaton(Q, 900 + Q)
+    seq = noisy_markov(901 + Q, 64 * MiB)
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    assert dfa.info().chunk_maps
+    c, p = gpu_run(dfa, to_device(seq, 5), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
+    c2, _ = gpu_run(dfa, to_device(seq, 5), positions=False)
+    assert c2 == want_c
+
+
+def test_non_converging_automaton_above_the_map_limit_is_exact():
+    """A 300-state permutation automaton is above the chunk-map limit (256 states): it is
+    scanned with speculation and repair, which walks the chunk boundaries in order and is
+    exact."""
+    table, acc = _permutation_automaton(300, 77)
+    seq = noisy_markov(78, 256 * 1024 + 9)
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    assert not dfa.info().chunk_maps
+    c, p = gpu_run(dfa, to_device(seq, 2), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
 
 
 def test_chunk_maps_forced_on_a_converging_regex():
