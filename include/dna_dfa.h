@@ -79,6 +79,23 @@ typedef struct dna_dfa dna_dfa; /* opaque; its tables live in device memory */
 int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t *accept_mask,
              dna_dfa **out);
 
+/*
+ * dfa_load_labeled -- dfa_load for an automaton that recognises several patterns at
+ * once and says which of them ends at each step. Alg. 1 of the paper keeps one counter
+ * per accepting state of its regex-dna automaton (the switch into final_states[] and
+ * the CR result struct) so that one scan gives a count per expression of Table V; here
+ * each state carries the set of patterns it reports.
+ *   table     as dfa_load.
+ *   labels    host uint32 [n_states]: bit i of labels[q] set <=> pattern i ends when a
+ *             step lands in q. F is the set of states with a non-zero mask.
+ *   n_labels  number of patterns, 1 .. 32; every mask must fit in n_labels bits.
+ * Every scan entry point accepts the handle (counting steps that land in F, whatever
+ * their labels); dna_scan_labels also reports per-label counts and label masks.
+ * Errors: as dfa_load; DNA_ERR_INVALID_ARG for a mask outside n_labels bits.
+ */
+int dfa_load_labeled(const uint32_t *table, uint32_t n_states, const uint32_t *labels,
+                     uint32_t n_labels, dna_dfa **out);
+
 /* dfa_free -- releases a handle (NULL is ignored). No scan using it may be in flight. */
 void dfa_free(dna_dfa *dfa);
 
@@ -90,6 +107,7 @@ typedef struct {
     uint32_t accept_start;     /* 1 when state 0 is in F */
     int32_t  device;
     uint32_t chunk_maps;       /* 1 when scans run every chunk from every state (see DNA_PLACE_MAP) */
+    uint32_t n_labels;         /* pattern labels (dfa_load_labeled), 0 for dfa_load */
 } dna_dfa_info;
 
 #define DNA_PLACE_AUTO       0
@@ -144,6 +162,26 @@ int dfa_analyze(const uint32_t *table, uint32_t n_states, int32_t *definite_dept
  */
 int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t stream,
              uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity);
+
+/*
+ * dna_scan_labels -- dna_scan with per-pattern results, for an automaton loaded with
+ * dfa_load_labeled (Alg. 1's count per accepting state, reported per pattern, Table V).
+ *   out_count         as dna_scan: steps that land in a state with any label.
+ *   out_label_counts  device uint64 [n_labels]: element i = steps that land in a state
+ *                     whose mask has bit i (a step reporting two patterns counts for
+ *                     both). Zeroed by the call on 'stream' before the scan adds to it.
+ *   out_positions     device or NULL: as dna_scan (ascending end positions, at most
+ *                     positions_capacity written).
+ *   out_pos_labels    device uint32 or NULL (needs out_positions): the label mask of
+ *                     each written position, same index.
+ * The per-label counts are exact whatever positions_capacity is: the extraction pass
+ * walks every row that holds a match. Asynchronous like dna_scan.
+ * Errors: DNA_ERR_INVALID_ARG (no labels on the handle, NULL outputs, out_pos_labels
+ * without out_positions), and as dna_scan.
+ */
+int dna_scan_labels(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t stream,
+                    uint64_t *out_count, uint64_t *out_label_counts, uint64_t *out_positions,
+                    uint32_t *out_pos_labels, uint64_t positions_capacity);
 
 /*
  * dna_scan_host -- dna_scan on a sequence in host memory, with host-memory results.
@@ -410,6 +448,13 @@ int dna_compile_regex(const char *pattern, uint32_t **table_out, uint8_t **accep
                       uint32_t *n_states_out);
 int dna_compile_kmers(const char *const *kmers, uint32_t n_kmers, uint32_t **table_out,
                       uint8_t **accept_out, uint32_t *n_states_out);
+/* dna_compile_regex_set: one minimal automaton for n_patterns (1 .. 32) regexes, the
+ * DFA of Sigma*.(L1 | ... | Ln) in which each state's label mask (labels_out, uint32 per
+ * state, for dfa_load_labeled) has bit i set when pattern i ends at a step landing in it
+ * (the paper scans the nine expressions of Table V with one automaton). States with
+ * different masks are never merged. Errors as dna_compile_regex. */
+int dna_compile_regex_set(const char *const *patterns, uint32_t n_patterns, uint32_t **table_out,
+                          uint32_t **labels_out, uint32_t *n_states_out);
 void dna_free_host(void *p);
 
 /*

@@ -61,6 +61,10 @@ def _load():
             lib.or_compile_kmers.restype = i32
             lib.or_minimise_table.argtypes = [p, p, i32, p, p, i32]
             lib.or_minimise_table.restype = i32
+            lib.or_compile_regex_set.argtypes = [cp, ctypes.c_int, p, p, i32]
+            lib.or_compile_regex_set.restype = i32
+            lib.or_run_labels.argtypes = [p, p, i32, p, i64, p, i32, p, p, i64]
+            lib.or_run_labels.restype = i64
             lib.or_symbol_of_byte.argtypes = [ctypes.c_int]
             lib.or_symbol_of_byte.restype = ctypes.c_int
             _lib = lib
@@ -135,6 +139,47 @@ def run(table: np.ndarray, accept: np.ndarray, seq, positions: bool = True,
                               s.ctypes.data, s.size, pos.ctypes.data, cap))
         if c <= cap:
             return c, pos[:c].copy()
+        cap = c
+
+
+def compile_regex_set(patterns, minimise: bool = True, cap: int = 4096):
+    """One DFA of Sigma*.(L1|...|Ln) for up to 32 regexes: (table int32 [Q,4], labels
+    uint32 [Q]) where bit i of labels[q] means pattern i ends at a step landing in q."""
+    arg = "\n".join(patterns).encode()
+    while True:
+        table = np.empty((cap, 4), dtype=np.int32)
+        lab = np.empty(cap, dtype=np.uint32)
+        rc = _load().or_compile_regex_set(arg, int(minimise), table.ctypes.data, lab.ctypes.data, cap)
+        if rc == -2 and cap < (1 << 24):
+            cap *= 4
+            continue
+        n = _check(rc)
+        return table[:n].copy(), lab[:n].copy()
+
+
+def run_labels(table: np.ndarray, labels: np.ndarray, n_labels: int, seq, positions: bool = True,
+               cap: int | None = None):
+    """The plain run with pattern labels: (count, per-label counts int64 [n_labels],
+    positions int64 or None, position masks uint32 or None)."""
+    table = np.ascontiguousarray(table, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.uint32)
+    s = _as_bytes(seq)
+    lib = _load()
+    counts = np.zeros(n_labels, dtype=np.int64)
+    if not positions:
+        c = _check(lib.or_run_labels(table.ctypes.data, labels.ctypes.data, table.shape[0], s.ctypes.data,
+                                     s.size, counts.ctypes.data, n_labels, None, None, 0))
+        return c, counts, None, None
+    if cap is None:
+        cap = 1024
+    while True:
+        pos = np.empty(cap, dtype=np.int64)
+        pl = np.empty(cap, dtype=np.uint32)
+        c = _check(lib.or_run_labels(table.ctypes.data, labels.ctypes.data, table.shape[0], s.ctypes.data,
+                                     s.size, counts.ctypes.data, n_labels, pos.ctypes.data, pl.ctypes.data,
+                                     cap))
+        if c <= cap:
+            return c, counts, pos[:c].copy(), pl[:c].copy()
         cap = c
 
 

@@ -426,18 +426,32 @@ static int subset_find_or_add(subset_ctx *c, const uint64_t *set, int final_stat
  * number the classes breadth-first from the class of q0, visiting A, C, G, T in order
  * (a canonical numbering: two minimal DFAs of the same language get equal tables).
  */
-static int moore_minimise(int n, const int32_t *trans, const uint8_t *acc,
-                          int32_t *out_table, uint8_t *out_acc, int cap)
+static int cmp_u32(const void *a, const void *b)
 {
-    int *cls = (int *)malloc(sizeof(int) * (size_t)n);
-    int *ncls = (int *)malloc(sizeof(int) * (size_t)n);
+    uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* The same refinement for states that carry a key (a pattern label mask): the starting
+ * partition puts states with equal keys together, so states that report different
+ * patterns are never merged. */
+static int moore_minimise_keys(int n, const int32_t *trans, const uint32_t *key,
+                               int32_t *out_table, uint32_t *out_key, int cap)
+{
+    int64_t *cls = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *ncls = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     int64_t *sig = (int64_t *)malloc(sizeof(int64_t) * 5 * (size_t)n);
     int *order = (int *)malloc(sizeof(int) * (size_t)n);
-    if (!cls || !ncls || !sig || !order) { free(cls); free(ncls); free(sig); free(order); return OR_ERR_NOMEM; }
-    int has_acc = 0, has_rej = 0;
-    for (int q = 0; q < n; q++) { cls[q] = acc[q] ? 1 : 0; if (acc[q]) has_acc = 1; else has_rej = 1; }
-    if (!has_rej) for (int q = 0; q < n; q++) cls[q] = 0;
-    int k = has_acc + has_rej;
+    uint32_t *keys = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!cls || !ncls || !sig || !order || !keys) {
+        free(cls); free(ncls); free(sig); free(order); free(keys); return OR_ERR_NOMEM;
+    }
+    /* the starting classes are the key values themselves; k = how many distinct ones */
+    for (int q = 0; q < n; q++) { cls[q] = key[q]; keys[q] = key[q]; }
+    qsort(keys, (size_t)n, sizeof(uint32_t), cmp_u32);
+    int k = n > 0 ? 1 : 0;
+    for (int i = 1; i < n; i++) if (keys[i] != keys[i - 1]) k++;
+    free(keys);
     for (;;) {
         /* signature of q = (class q, class of each successor); classes are then the
          * distinct signatures, numbered by first appearance in a sorted order. */
@@ -479,12 +493,13 @@ static int moore_minimise(int n, const int32_t *trans, const uint8_t *acc,
             ncls[q] = nk;
         }
         nk++;
-        memcpy(cls, ncls, sizeof(int) * (size_t)n);
+        memcpy(cls, ncls, sizeof(int64_t) * (size_t)n);
         if (nk == k) break;
         k = nk;
     }
     if (k > cap) { free(cls); free(ncls); free(sig); free(order); return OR_ERR_CAPACITY; }
     /* canonical breadth-first numbering from the class of q0 */
+    /* after the loop the classes are numbered 0..k-1 */
     int *rep = (int *)malloc(sizeof(int) * (size_t)k);   /* a member state of each class */
     int *newid = (int *)malloc(sizeof(int) * (size_t)k);
     int *queue = (int *)malloc(sizeof(int) * (size_t)k);
@@ -502,12 +517,26 @@ static int moore_minimise(int n, const int32_t *trans, const uint8_t *acc,
     int reach = tail;
     for (int i = 0; i < reach; i++) {
         int c = queue[i];
-        out_acc[i] = acc[rep[c]];
+        out_key[i] = key[rep[c]];
         for (int s = 0; s < 4; s++) out_table[4 * i + s] = newid[cls[trans[4 * rep[c] + s]]];
     }
     free(rep); free(newid); free(queue);
     free(cls); free(ncls); free(sig); free(order);
     return reach;
+}
+
+/* Moore minimisation with accept flags (0/1): the keyed refinement on {F, Q \ F}. */
+static int moore_minimise(int n, const int32_t *trans, const uint8_t *acc,
+                          int32_t *out_table, uint8_t *out_acc, int cap)
+{
+    uint32_t *key = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t *okey = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    if (!key || !okey) { free(key); free(okey); return OR_ERR_NOMEM; }
+    for (int q = 0; q < n; q++) key[q] = acc[q] ? 1u : 0u;
+    int r = moore_minimise_keys(n, trans, key, out_table, okey, cap);
+    for (int i = 0; i < r; i++) out_acc[i] = (uint8_t)okey[i];
+    free(key); free(okey);
+    return r;
 }
 
 /* ------------------------------------------------------ regex -> DFA (public) */
@@ -589,6 +618,156 @@ int32_t or_compile_regex(const char *pattern, int minimise, int32_t *table_out,
     free(stack); free(tmp); free(a.st);
     free(c.bits); free(c.trans); free(c.acc); free(c.hash_next); free(c.hash_head);
     return result;
+}
+
+/* -------------------------------------- several patterns with labels (public) */
+
+/*
+ * One automaton for several regexes, as the paper scans the nine regex-dna expressions
+ * of Table V with one DFA and keeps a counter per accepting state (Alg. 1, the switch
+ * into final_states[]): the NFA has one Sigma* loop in front of every pattern, each
+ * pattern keeps its own exit state, and a DFA state's label mask has bit i set when
+ * pattern i's exit state is in its NFA set. 'patterns' holds up to 32 regexes separated
+ * by newlines. minimise = 1 applies the keyed Moore refinement from the partition by
+ * label mask. Returns the number of states or < 0.
+ */
+int32_t or_compile_regex_set(const char *patterns, int minimise, int32_t *table_out,
+                             uint32_t *labels_out, int32_t cap_states)
+{
+    if (!patterns || !table_out || !labels_out || cap_states <= 0) return OR_ERR_ARG;
+    nfa a; memset(&a, 0, sizeof(a));
+    int loop = nfa_new(&a);
+    int hook = loop;   /* every pattern start hangs off a chain of fork states (two eps each) */
+    int exits[32], n_pat = 0, rc = 0;
+    const char *p = patterns;
+    char *buf = (char *)malloc(strlen(patterns) + 1);
+    if (!buf) { free(a.st); return OR_ERR_NOMEM; }
+    while (!rc) {
+        const char *e = strchr(p, '\n');
+        size_t len = e ? (size_t)(e - p) : strlen(p);
+        if (n_pat == 32) { rc = OR_ERR_ARG; break; }
+        memcpy(buf, p, len); buf[len] = '\0';
+        rx_parser ps; memset(&ps, 0, sizeof(ps));
+        ps.p = buf;
+        int root = rx_alt(&ps);
+        if (!ps.err && *ps.p != '\0') ps.err = OR_ERR_SYNTAX;
+        if (ps.err) { rc = ps.err; free(ps.nodes); break; }
+        int pout, pstart = nfa_build(&a, ps.nodes, root, &pout);
+        free(ps.nodes);
+        int fork = nfa_new(&a);
+        if (a.err) { rc = a.err; break; }
+        nfa_eps(&a, hook, fork);
+        nfa_eps(&a, fork, pstart);
+        hook = fork;
+        exits[n_pat++] = pout;
+        if (!e) break;
+        p = e + 1;
+    }
+    free(buf);
+    if (rc) { free(a.st); return rc; }
+    a.st[loop].set = 15; a.st[loop].to = loop;   /* the Sigma* self-loop */
+
+    int words = (a.n + 63) / 64;
+    int *stack = (int *)malloc(sizeof(int) * (size_t)a.n * 2);
+    uint64_t *tmp = (uint64_t *)calloc((size_t)words, sizeof(uint64_t));
+    subset_ctx c; memset(&c, 0, sizeof(c));
+    c.words = words; c.cap = 256; c.hash_size = 1 << 16;
+    c.bits = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)c.cap * words);
+    c.trans = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)c.cap);
+    c.acc = (uint8_t *)malloc((size_t)c.cap);
+    c.hash_next = (int *)malloc(sizeof(int) * (size_t)c.cap);
+    c.hash_head = (int *)malloc(sizeof(int) * (size_t)c.hash_size);
+    if (!stack || !tmp || !c.bits || !c.trans || !c.acc || !c.hash_next || !c.hash_head) rc = OR_ERR_NOMEM;
+    if (!rc) {
+        for (int i = 0; i < c.hash_size; i++) c.hash_head[i] = -1;
+        tmp[loop >> 6] |= 1ull << (loop & 63);
+        eps_closure(&a, tmp, stack);
+        for (int i = 0; i < n_pat; i++)
+            if ((tmp[exits[i] >> 6] >> (exits[i] & 63)) & 1) rc = OR_ERR_EMPTYWORD;
+    }
+    if (!rc) {
+        int added;
+        subset_find_or_add(&c, tmp, exits[0], &added);
+        for (int d = 0; d < c.n && !rc; d++) {
+            for (int s = 0; s < 4 && !rc; s++) {
+                memset(tmp, 0, sizeof(uint64_t) * words);
+                const uint64_t *cur = c.bits + (size_t)d * words;
+                for (int u = 0; u < a.n; u++)
+                    if ((cur[u >> 6] >> (u & 63) & 1) && (a.st[u].set >> s & 1)) {
+                        int v = a.st[u].to;
+                        tmp[v >> 6] |= 1ull << (v & 63);
+                    }
+                eps_closure(&a, tmp, stack);
+                int id = subset_find_or_add(&c, tmp, exits[0], &added);
+                if (id < 0) { rc = id; break; }
+                c.trans[4 * d + s] = id;
+                if (c.n > (1 << 22)) rc = OR_ERR_CAPACITY;
+            }
+        }
+    }
+    int32_t result = rc;
+    uint32_t *lab = NULL;
+    if (!rc) {
+        /* label mask of every DFA state: which patterns' exit states its set holds */
+        lab = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)c.n);
+        if (!lab) result = OR_ERR_NOMEM;
+        else {
+            for (int d = 0; d < c.n; d++) {
+                const uint64_t *set = c.bits + (size_t)d * words;
+                uint32_t m = 0;
+                for (int i = 0; i < n_pat; i++)
+                    if ((set[exits[i] >> 6] >> (exits[i] & 63)) & 1) m |= 1u << i;
+                lab[d] = m;
+            }
+            if (minimise) {
+                result = moore_minimise_keys(c.n, c.trans, lab, table_out, labels_out, cap_states);
+            } else if (c.n > cap_states) {
+                result = OR_ERR_CAPACITY;
+            } else {
+                memcpy(table_out, c.trans, sizeof(int32_t) * 4 * (size_t)c.n);
+                memcpy(labels_out, lab, sizeof(uint32_t) * (size_t)c.n);
+                result = c.n;
+            }
+        }
+    }
+    free(lab);
+    free(stack); free(tmp); free(a.st);
+    free(c.bits); free(c.trans); free(c.acc); free(c.hash_next); free(c.hash_head);
+    return result;
+}
+
+/*
+ * The plain run with labels (Alg. 1's count per accepting state, reported per pattern):
+ * one transition per byte from q0, reset bytes to state 0; a step whose post-transition
+ * state has a non-zero mask counts once in the total and once for every pattern in the
+ * mask. Writes at most pos_cap positions and masks; returns the total count.
+ */
+int64_t or_run_labels(const int32_t *table, const uint32_t *labels, int32_t n_states,
+                      const uint8_t *seq, int64_t n, int64_t *label_counts, int32_t n_labels,
+                      int64_t *pos_out, uint32_t *pos_lab_out, int64_t pos_cap)
+{
+    if (n_states <= 0 || !table || !labels || !label_counts || n_labels <= 0 || n_labels > 32 ||
+        (n > 0 && !seq)) return OR_ERR_ARG;
+    for (int i = 0; i < n_labels; i++) label_counts[i] = 0;
+    int32_t q = 0;
+    int64_t count = 0;
+    for (int64_t j = 0; j < n; j++) {
+        int s = or_symbol_of_byte(seq[j]);
+        if (s == 4) q = 0;
+        else q = table[(int64_t)q * 4 + s];
+        if (q < 0 || q >= n_states) return OR_ERR_ARG;
+        uint32_t m = labels[q];
+        if (m) {
+            if (pos_out && count < pos_cap) {
+                pos_out[count] = j;
+                if (pos_lab_out) pos_lab_out[count] = m;
+            }
+            count++;
+            for (int i = 0; i < n_labels; i++)
+                if ((m >> i) & 1u) label_counts[i]++;
+        }
+    }
+    return count;
 }
 
 /* ------------------------------------------------- Aho-Corasick (public) */

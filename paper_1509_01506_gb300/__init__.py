@@ -23,7 +23,8 @@ PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE, PLACE_MAP = 0, 1,
 
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
-    "dna_scan_count_static", "dna_scan_host",
+    "dna_scan_count_static", "dna_scan_host", "dfa_load_labeled", "dna_scan_labels",
+    "dna_compile_regex_set",
     "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
     "dna_server_create", "dna_server_submit", "dna_server_poll", "dna_server_drain",
     "dna_server_stats", "dna_server_now_ns", "dna_server_free", "dna_fasta_parse",
@@ -43,7 +44,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("n_states", ctypes.c_uint32), ("definite_depth", ctypes.c_int32),
                 ("lookback", ctypes.c_uint32), ("placement", ctypes.c_uint32),
                 ("accept_start", ctypes.c_uint32), ("device", ctypes.c_int32),
-                ("chunk_maps", ctypes.c_uint32)]
+                ("chunk_maps", ctypes.c_uint32), ("n_labels", ctypes.c_uint32)]
 
 
 class _Plan(ctypes.Structure):
@@ -130,6 +131,12 @@ def lib():
         L.dna_scan_count_static.restype = i32
         L.dna_scan_host.argtypes = [p, p, u64, p, p, p, u64]
         L.dna_scan_host.restype = i32
+        L.dfa_load_labeled.argtypes = [p, u32, p, u32, ctypes.POINTER(p)]
+        L.dfa_load_labeled.restype = i32
+        L.dna_scan_labels.argtypes = [p, p, u64, p, p, p, p, p, u64]
+        L.dna_scan_labels.restype = i32
+        L.dna_compile_regex_set.argtypes = [p, u32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(u32)]
+        L.dna_compile_regex_set.restype = i32
         L.dna_batch_create.argtypes = [p, u32, p, p, u32, ctypes.POINTER(_BatchOpts), p, ctypes.POINTER(p)]
         L.dna_batch_create.restype = i32
         L.dna_batch_run.argtypes = [p, p, p]
@@ -216,6 +223,25 @@ def compile_kmers(kmers):
     return _take_table(tp, ap, n.value)
 
 
+def compile_regex_set(patterns):
+    """Host compiler for several patterns at once: (table uint32 [Q,4], labels uint32 [Q])
+    where bit i of labels[q] means pattern i ends at a step landing in q."""
+    arr = (ctypes.c_char_p * len(patterns))(*[p.encode() for p in patterns])
+    tp, lp, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_uint32()
+    L = lib()
+    _check(L.dna_compile_regex_set(ctypes.cast(arr, ctypes.c_void_p), len(patterns), ctypes.byref(tp),
+                                   ctypes.byref(lp), ctypes.byref(n)), "compile_regex_set")
+    try:
+        table = np.ctypeslib.as_array(ctypes.cast(tp, ctypes.POINTER(ctypes.c_uint32)),
+                                      shape=(n.value, 4)).copy()
+        labels = np.ctypeslib.as_array(ctypes.cast(lp, ctypes.POINTER(ctypes.c_uint32)),
+                                       shape=(n.value,)).copy()
+    finally:
+        L.dna_free_host(tp)
+        L.dna_free_host(lp)
+    return table, labels
+
+
 def fasta_parse(text: bytes):
     """dna_fasta_parse: (sequence bytes as a uint8 array, record offsets [n+1], headers).
     Record r is seq[offsets[r]:offsets[r+1]]."""
@@ -258,24 +284,44 @@ class DfaInfo:
     accept_start: bool
     device: int
     chunk_maps: bool
+    n_labels: int = 0
 
 
 class Dfa:
-    """A device-resident automaton (dfa_load / dfa_free)."""
+    """A device-resident automaton (dfa_load / dfa_free; dfa_load_labeled when 'labels'
+    is given: uint32 [n_states] pattern masks over n_labels patterns)."""
 
-    def __init__(self, table, accept_mask):
+    def __init__(self, table, accept_mask=None, labels=None, n_labels: int = 0):
         table = np.ascontiguousarray(table, dtype=np.uint32)
-        mask = np.ascontiguousarray(accept_mask, dtype=np.uint8)
         if table.ndim != 2 or table.shape[1] != 4:
             raise ValueError("table must be [n_states, 4]")
         n = table.shape[0]
-        if mask.size < (n + 7) // 8:
-            raise ValueError("accept mask too short")
         h = ctypes.c_void_p()
-        _check(lib().dfa_load(table.ctypes.data, n, mask.ctypes.data, ctypes.byref(h)), "dfa_load")
+        if labels is not None:
+            lab = np.ascontiguousarray(labels, dtype=np.uint32)
+            if lab.size != n:
+                raise ValueError("labels must have one mask per state")
+            if not n_labels:
+                n_labels = max(1, int(lab.max()).bit_length())
+            _check(lib().dfa_load_labeled(table.ctypes.data, n, lab.ctypes.data, n_labels, ctypes.byref(h)),
+                   "dfa_load_labeled")
+            mask = pack_accept(lab != 0)
+            self.labels = lab
+        else:
+            mask = np.ascontiguousarray(accept_mask, dtype=np.uint8)
+            if mask.size < (n + 7) // 8:
+                raise ValueError("accept mask too short")
+            _check(lib().dfa_load(table.ctypes.data, n, mask.ctypes.data, ctypes.byref(h)), "dfa_load")
+            self.labels = None
         self._h = h
         self.table = table
         self.accept_mask = mask
+
+    @classmethod
+    def from_regex_set(cls, patterns) -> "Dfa":
+        """One automaton for several regexes, each step labelled with the patterns ending there."""
+        table, labels = compile_regex_set(list(patterns))
+        return cls(table, labels=labels, n_labels=len(patterns))
 
     @classmethod
     def from_regex(cls, pattern: str) -> "Dfa":
@@ -295,7 +341,7 @@ class Dfa:
         i = _Info()
         _check(lib().dfa_info(self.handle, ctypes.byref(i)), "dfa_info")
         return DfaInfo(i.n_states, i.definite_depth, i.lookback, i.placement,
-                       bool(i.accept_start), i.device, bool(i.chunk_maps))
+                       bool(i.accept_start), i.device, bool(i.chunk_maps), i.n_labels)
 
     def free(self):
         if self._h:
@@ -351,6 +397,32 @@ def scan(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None,
                         pos_ptr, cap)
     _check(rc, "dna_scan")
     return out_count, (out_positions if positions else None)
+
+
+def scan_labels(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None, stream=None):
+    """dna_scan_labels on a CUDA uint8 tensor (automaton from dfa_load_labeled). Returns
+    (count [1], per-label counts [n_labels] int64, positions or None, position label masks
+    (int32) or None). Results are ready when the stream completes."""
+    import torch
+    if not (isinstance(seq, torch.Tensor) and seq.is_cuda and seq.dtype == torch.uint8):
+        raise TypeError("seq must be a CUDA uint8 tensor")
+    if not seq.is_contiguous():
+        raise ValueError("seq must be contiguous")
+    dev = seq.device
+    n_labels = dfa.info().n_labels
+    count = torch.empty(1, dtype=torch.int64, device=dev)
+    lab = torch.empty(max(1, n_labels), dtype=torch.int64, device=dev)
+    pos = pos_lab = None
+    cap = 0
+    if positions:
+        cap = int(capacity if capacity is not None else max(1024, seq.numel() // 256))
+        pos = torch.empty(cap, dtype=torch.int64, device=dev)
+        pos_lab = torch.empty(cap, dtype=torch.int32, device=dev)
+    _check(lib().dna_scan_labels(dfa.handle, seq.data_ptr(), seq.numel(), _stream_handle(stream),
+                                 count.data_ptr(), lab.data_ptr(),
+                                 pos.data_ptr() if positions else None,
+                                 pos_lab.data_ptr() if positions else None, cap), "dna_scan_labels")
+    return count, lab[:n_labels], pos, pos_lab
 
 
 def scan_ptr(dfa: Dfa, ptr: int, length: int, out_count_ptr: int, stream_handle: int,

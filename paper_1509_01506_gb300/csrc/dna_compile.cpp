@@ -193,7 +193,10 @@ struct Info { bool nullable; Bits first, last; };
 
 void bits_or(Bits &a, const Bits &b) { for (size_t k = 0; k < a.size(); ++k) a[k] |= b[k]; }
 
-void build_glushkov(const std::vector<Node> &nodes, int root, Glushkov &g) {
+// 'roots_last' (optional): receives the last-position set of each listed subtree.
+void build_glushkov(const std::vector<Node> &nodes, int root, Glushkov &g,
+                    const std::vector<int> *roots = nullptr, std::vector<Bits> *roots_last = nullptr,
+                    std::vector<bool> *roots_nullable = nullptr) {
     // assign positions to leaves reachable from root (iterative post-order)
     std::vector<int> order, stack{root};
     while (!stack.empty()) {
@@ -245,13 +248,23 @@ void build_glushkov(const std::vector<Node> &nodes, int root, Glushkov &g) {
     g.first = info[root].first;
     g.last = info[root].last;
     g.nullable = info[root].nullable;
+    if (roots && roots_last) {
+        roots_last->clear();
+        if (roots_nullable) roots_nullable->clear();
+        for (int r : *roots) {
+            roots_last->push_back(info[r].last);
+            if (roots_nullable) roots_nullable->push_back(info[r].nullable);
+        }
+    }
 }
 
 // Direct subset construction of Sigma*.L over Glushkov positions: a DFA state is the
 // set of positions that the last symbol can have matched. On base c the next set is
 // every position p labelled with c that is either a first position (the Sigma* prefix
 // lets a match start anywhere) or follows a position in the current set.
-int glushkov_dfa(const Glushkov &g, HostDfa &out) {
+// 'lasts' (optional) holds one last-position set per pattern of a union: a DFA state's
+// accept mask then has bit i set when its set meets pattern i's last positions.
+int glushkov_dfa(const Glushkov &g, HostDfa &out, const std::vector<Bits> *lasts = nullptr) {
     size_t words = (size_t)(g.n_pos + 63) / 64;
     std::map<Bits, uint32_t> ids;
     std::vector<Bits> sets;
@@ -276,10 +289,20 @@ int glushkov_dfa(const Glushkov &g, HostDfa &out) {
                 id = (uint32_t)sets.size();
                 if (id >= (1u << 22)) return DNA_ERR_CAPACITY;
                 ids.emplace(nx, id);
-                bool acc = false;
-                for (size_t k = 0; k < words; ++k) acc |= (nx[k] & g.last[k]) != 0;
+                uint32_t mask = 0;
+                if (lasts) {
+                    for (size_t i = 0; i < lasts->size(); ++i) {
+                        bool hit = false;
+                        for (size_t k = 0; k < words; ++k) hit |= (nx[k] & (*lasts)[i][k]) != 0;
+                        if (hit) mask |= 1u << i;
+                    }
+                } else {
+                    bool acc = false;
+                    for (size_t k = 0; k < words; ++k) acc |= (nx[k] & g.last[k]) != 0;
+                    mask = acc ? 1u : 0u;
+                }
                 sets.push_back(nx);
-                out.accept.push_back(acc ? 1 : 0);
+                out.accept.push_back(mask);
             } else {
                 id = it->second;
             }
@@ -308,16 +331,18 @@ int hopcroft(const HostDfa &in, HostDfa &out) {
     std::vector<uint32_t> elems(n), where(n), block(n);
     std::vector<uint32_t> bstart, bend, marked;
     {
+        // one initial block per distinct accept mask (for a single pattern: F and Q \ F)
+        std::vector<uint32_t> masks(in.accept.begin(), in.accept.begin() + n);
+        std::sort(masks.begin(), masks.end());
+        masks.erase(std::unique(masks.begin(), masks.end()), masks.end());
         uint32_t k = 0;
-        for (int pass = 0; pass < 2; ++pass) {
+        for (uint32_t m : masks) {
             uint32_t st = k;
             for (uint32_t s = 0; s < n; ++s)
-                if ((in.accept[s] != 0) == (pass == 1)) { elems[k] = s; where[s] = k; ++k; }
-            if (k > st) {
-                uint32_t b = (uint32_t)bstart.size();
-                bstart.push_back(st); bend.push_back(k); marked.push_back(0);
-                for (uint32_t i = st; i < k; ++i) block[elems[i]] = b;
-            }
+                if (in.accept[s] == m) { elems[k] = s; where[s] = k; ++k; }
+            uint32_t b = (uint32_t)bstart.size();
+            bstart.push_back(st); bend.push_back(k); marked.push_back(0);
+            for (uint32_t i = st; i < k; ++i) block[elems[i]] = b;
         }
     }
     std::vector<std::vector<uint8_t>> in_work;
@@ -414,6 +439,36 @@ int compile_regex(const char *pattern, HostDfa &out) {
     return hopcroft(raw, out);
 }
 
+int compile_regex_set(const std::vector<std::string> &patterns, HostDfa &out) {
+    if (patterns.empty() || patterns.size() > 32) return DNA_ERR_INVALID_ARG;
+    Parser ps;
+    std::vector<int> roots;
+    for (const std::string &pat : patterns) {
+        ps.s = pat.c_str();
+        ps.i = 0;
+        int r = ps.alt();
+        if (!ps.err && pat[ps.i] != '\0') ps.err = DNA_ERR_SYNTAX;
+        if (ps.err) return ps.err;
+        roots.push_back(r);
+    }
+    // the union of the patterns: every pattern keeps its own positions
+    int root = roots[0];
+    for (size_t i = 1; i < roots.size(); ++i) {
+        Node n; n.kind = ALT; n.a = root; n.b = roots[i];
+        root = ps.add(n);
+    }
+    Glushkov g;
+    std::vector<Bits> lasts;
+    std::vector<bool> nullable;
+    build_glushkov(ps.nodes, root, g, &roots, &lasts, &nullable);
+    for (bool nb : nullable)
+        if (nb) return DNA_ERR_EMPTY_WORD;
+    HostDfa raw;
+    int rc = glushkov_dfa(g, raw, &lasts);
+    if (rc) return rc;
+    return hopcroft(raw, out);
+}
+
 int compile_kmers(const std::vector<std::string> &kmers, HostDfa &out) {
     if (kmers.empty()) return DNA_ERR_INVALID_ARG;
     std::vector<std::array<int32_t, 4>> go(1);
@@ -450,7 +505,7 @@ int compile_kmers(const std::vector<std::string> &kmers, HostDfa &out) {
     }
     for (size_t h = 0; h < order.size(); ++h) {
         uint32_t q = order[h];
-        raw.accept[q] = (uint8_t)(term[q] | raw.accept[fail[q]]);
+        raw.accept[q] = (uint32_t)(term[q] | raw.accept[fail[q]]);
         for (int c = 0; c < 4; ++c) {
             uint32_t via_fail = raw.table[4 * (size_t)fail[q] + c];
             if (go[q][c] >= 0) {
@@ -567,6 +622,34 @@ extern "C" int dna_compile_kmers(const char *const *kmers, uint32_t n_kmers,
         int rc = dnalib::compile_kmers(v, d);
         if (rc) return rc;
         return export_dfa(d, table_out, accept_out, n_states_out);
+    } catch (const std::bad_alloc &) {
+        return DNA_ERR_NOMEM;
+    }
+}
+
+extern "C" int dna_compile_regex_set(const char *const *patterns, uint32_t n_patterns,
+                                     uint32_t **table_out, uint32_t **labels_out,
+                                     uint32_t *n_states_out) {
+    if (!patterns || n_patterns == 0 || n_patterns > 32 || !table_out || !labels_out || !n_states_out)
+        return DNA_ERR_INVALID_ARG;
+    try {
+        std::vector<std::string> v;
+        for (uint32_t i = 0; i < n_patterns; ++i) {
+            if (!patterns[i]) return DNA_ERR_INVALID_ARG;
+            v.emplace_back(patterns[i]);
+        }
+        dnalib::HostDfa d;
+        int rc = dnalib::compile_regex_set(v, d);
+        if (rc) return rc;
+        uint32_t *t = (uint32_t *)malloc(sizeof(uint32_t) * 4 * (size_t)d.n_states);
+        uint32_t *l = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)d.n_states);
+        if (!t || !l) { free(t); free(l); return DNA_ERR_NOMEM; }
+        memcpy(t, d.table.data(), sizeof(uint32_t) * 4 * (size_t)d.n_states);
+        memcpy(l, d.accept.data(), sizeof(uint32_t) * (size_t)d.n_states);
+        *table_out = t;
+        *labels_out = l;
+        *n_states_out = d.n_states;
+        return DNA_OK;
     } catch (const std::bad_alloc &) {
         return DNA_ERR_NOMEM;
     }

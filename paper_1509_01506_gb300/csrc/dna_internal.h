@@ -9,15 +9,19 @@
 namespace dnalib {
 
 // Complete DFA in the dfa_load layout: table[q*4 + s], s = 0..3 for A, C, G, T;
-// accept[q] = 0/1; state 0 is the start state.
+// accept[q] = the set of patterns that end when a step lands in q, as a bit mask (0 or
+// 1 for a single pattern); state 0 is the start state.
 struct HostDfa {
     std::vector<uint32_t> table;
-    std::vector<uint8_t> accept;
+    std::vector<uint32_t> accept;
     uint32_t n_states = 0;
 };
 
 // Each returns a DNA_* status code.
 int compile_regex(const char *pattern, HostDfa &out);
+// One automaton for several patterns (at most 32): accept[q] has bit i set when pattern
+// i ends at a step that lands in q. Minimisation keeps states with different masks apart.
+int compile_regex_set(const std::vector<std::string> &patterns, HostDfa &out);
 int compile_kmers(const std::vector<std::string> &kmers, HostDfa &out);
 int minimise(const HostDfa &in, HostDfa &out);
 

@@ -355,7 +355,7 @@ namespace dnalib {
 // ceil(Q / 32) warps per chunk. 'ext' (count only) supplies the scratch instead of the
 // library's pool: ext_bytes of device memory; DNA_ERR_CAPACITY when it is too small.
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream, uint64_t *out_count,
-                  uint64_t *out_positions, uint64_t cap, uint8_t *ext, size_t ext_bytes) {
+                  uint64_t *out_positions, uint64_t cap, uint8_t *ext, size_t ext_bytes, const LabelOut *lab) {
     if (d->n_states > kMaxMapStates) return DNA_ERR_INVALID_ARG;
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;
@@ -372,7 +372,8 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     uint64_t S = (total + want_chunks - 1) / want_chunks;
     S = (S + unit - 1) / unit * unit;
     const uint32_t n_chunks = (uint32_t)((total + S - 1) / S);
-    const bool positions = out_positions != nullptr && cap > 0;
+    // the positions pass also gives per-label outputs
+    const bool positions = (out_positions != nullptr && cap > 0) || lab != nullptr;
     if (ext && positions) return DNA_ERR_INVALID_ARG;
     const size_t nq = (size_t)n_chunks * qp;
     size_t off = 0;
@@ -442,7 +443,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
         dna_plan pl = {};
         pl.chunk_bytes = (uint32_t)(S / kMapSubs);
         pl.placement = d->d_pair ? DNA_PLACE_SMEM_PAIR : 0u;
-        rc = scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, &pl, jp.given);
+        rc = scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, &pl, jp.given, lab);
     }
     if (!ext) {
         const int rf = scratch_free(mem, stream);

@@ -23,6 +23,8 @@ struct dna_dfa {
     uint32_t *d_one = nullptr;    // [n_states][4] one-symbol entries, code order A, C, T, G
     uint32_t *d_pair = nullptr;   // [n_states][16] compact pair entries (small automata)
     bool map_mode = false;        // scans use chunk maps (runs from different states do not meet)
+    uint32_t *d_labels = nullptr; // [n_states] label mask of each state (dfa_load_labeled), or null
+    uint32_t n_labels = 0;
     // resident blocks per SM of each scan kernel variant with this automaton's shared
     // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
     std::atomic<int> per_sm[3][4][2] = {};
@@ -60,21 +62,32 @@ cudaError_t device_alloc(void **p, size_t bytes);
 // pool_alloc: a (counted) stream-ordered allocation from a pool the caller owns.
 cudaError_t pool_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t s);
 
+// Per-label outputs of a scan (dna_scan_labels): the extraction pass walks every hit row
+// and adds each accepting step's label mask into 'counts' (device, zeroed by the caller);
+// 'pos_labels' (device or null) receives each written position's mask.
+struct LabelOut {
+    const uint32_t *labels = nullptr;   // [n_states] device label masks
+    unsigned long long *counts = nullptr;
+    uint32_t *pos_labels = nullptr;
+    uint32_t n_labels = 0;
+};
+
 // The single-sequence scan behind dna_scan / dna_scan_planned (dispatches to the
-// chunk-map path for automata that need it).
+// chunk-map path for automata that need it). 'lab' (or null) asks for per-label outputs.
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
-              uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov);
+              uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
+              const LabelOut *lab = nullptr);
 // The speculative chunk scan; 'given_start' (per chunk, or null) supplies exact chunk
 // start states, in which case nothing is speculated or repaired.
 int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                     uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
-                    const uint32_t *given_start);
+                    const uint32_t *given_start, const LabelOut *lab = nullptr);
 // The chunk-map scan (dna_map.cu); n_states <= kMaxMapStates. 'ext' (count only, or
 // null) is caller-provided scratch of ext_bytes bytes used instead of the library's pool.
 constexpr uint32_t kMaxMapStates = 256;
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                   uint64_t *out_count, uint64_t *out_positions, uint64_t cap,
-                  uint8_t *ext = nullptr, size_t ext_bytes = 0);
+                  uint8_t *ext = nullptr, size_t ext_bytes = 0, const LabelOut *lab = nullptr);
 
 // Kernel timing: prof_begin records an event on the stream when profiling is enabled
 // (otherwise returns an empty token); prof_end records the closing event.

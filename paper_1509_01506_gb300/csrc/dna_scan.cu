@@ -64,6 +64,12 @@ struct EmitParams {
     uint64_t *out;
     uint64_t cap;
     uint32_t lut_lo, lut_hi;   // expected lowercase bytes per code, for the base check
+    // per-label outputs (null labels: none): every hit row is walked, whatever the
+    // capacity, and each accepting step's label mask is added into label_counts
+    const uint32_t *labels;
+    unsigned long long *label_counts;
+    uint32_t *pos_labels;
+    uint32_t n_labels;
 };
 
 constexpr int kEmitWalkers = 256;    // threads of an extraction block that walk rows
@@ -155,6 +161,70 @@ __device__ __forceinline__ bool walk_row_pairs(const EmitParams &p, const uint32
     return true;
 }
 
+// The two-symbol row walk that also follows the state: the same walk over a whole row
+// of bases (returns false, writing nothing, when the row holds a non-base byte and is not
+// 'checked'), writing positions as it goes. With per-label outputs a pair with an
+// accepting step resolves the state of that step (after the pair's second symbol: the
+// entry's next state; after its first: one extra one-symbol lookup) and its label mask,
+// writes the mask beside the position and adds it into the walker's counters 'wl' (label
+// i at wl[i * kEmitWalkers]). 'q' is the state before the row and, after a walk, the
+// state after it (rescans continue from it).
+__device__ __forceinline__ bool walk_row_pairs_lab(const EmitParams &p, const uint32_t *ptab, uint64_t rs,
+                                                   uint32_t &q, unsigned long long &o, bool checked,
+                                                   uint32_t *wl) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.abase + rs);
+    if (!checked) {
+        uint32_t err = 0;
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const uint4 v = src[h];
+            const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t x = ww[i] & 0x06060606u;
+                const uint32_t z = x | (x >> 4);
+                err |= __byte_perm(p.lut_lo, p.lut_hi, __byte_perm(z, 0, 0x0020)) ^ ww[i];
+            }
+        }
+        if (err & 0xDFDFDFDFu) return false;
+    }
+    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(ptab);
+    const uint64_t pos0 = rs - p.lo;
+    auto hit = [&](uint64_t pos, uint32_t m) {   // m: label mask (0 without labels)
+        if (o < p.cap) {
+            p.out[o] = pos;
+            if (p.pos_labels) p.pos_labels[o] = m;
+        }
+        ++o;
+        while (m) {
+            wl[(__ffs(m) - 1) * kEmitWalkers] += 1u;
+            m &= m - 1;
+        }
+    };
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+        const uint4 v = src[h];
+        const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t y = (ww[i] & 0x06060606u) * 65u;   // pair codes at bits 7..10, 23..26
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint32_t pc = (y >> (j ? 23 : 7)) & 15u;
+                const uint32_t e = lds_u32(pbase + (q * 16u + pc) * 4u);
+                if (e >> 30) {
+                    const uint64_t pos = pos0 + 16u * h + 4u * i + 2u * j;
+                    if (e & 0x40000000u)
+                        hit(pos, p.labels ? p.labels[p.one[q * 4u + (pc & 3u)] & 0x7FFFFFFFu] : 0u);
+                    if (e >> 31) hit(pos + 1, p.labels ? p.labels[e & 0x3FFFFFFFu] : 0u);
+                }
+                q = e & 0x3FFFFFFFu;
+            }
+        }
+    }
+    return true;
+}
+
 // Record i of chunk c as the true run's: records are written by the speculative run; a
 // chunk repaired at its converging point inside row 0 (kFlagFixed) takes its row-0 start
 // from the true start and moves later rows' count offsets by its delta, and when the
@@ -180,6 +250,7 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     __shared__ uint8_t s_rescan[1024];
     __shared__ uint4 s_rec[kEmitRecs];   // (tile, start state, count before, chunk index)
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const bool lab = p.labels != nullptr;
     // dynamic shared memory: [row slots: walkers x pitch][offsets: nthr x 8][fix: nthr x 8]
     //                        [slots: nthr+1 x 4][tables]
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(dsm + kEmitWalkers * kEmitRowPitch);
@@ -187,6 +258,10 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     uint32_t *s_slot = reinterpret_cast<uint32_t *>(s_fix + nthr);
     uint32_t *tab5 = s_slot + nthr + 1;
     uint32_t *ptab = tab5 + (tab5_in_smem ? p.n_states * 5u : 0u);
+    // per-label outputs: each walker's own counters, [label][walker]
+    uint32_t *s_wlab = ptab + (ptab_in_smem ? p.n_states * 16u : 0u);
+    if (lab)
+        for (uint32_t i = tid; i < 32u * kEmitWalkers; i += nthr) s_wlab[i] = 0;
     if (tid < 256) {
         const uint32_t c = (tid >> 1) & 3u;
         cls[tid] = byte_is_base(tid) ? (uint8_t)c : (uint8_t)4;
@@ -269,6 +344,16 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             const uint32_t e = tab ? tab[q * 5u + cl] : (cl < 4 ? p.one[q * 4u + cl] : p.reset_entry);
             q = e & 0x7FFFFFFFu;
             if (e >> 31) {
+                if (lab) {
+                    // the pattern labels of the state this step lands in
+                    uint32_t m = p.labels[q];
+                    if (o < p.cap && p.pos_labels) p.pos_labels[o] = m;
+                    uint32_t *wl = s_wlab + tid;
+                    while (m) {
+                        wl[(__ffs(m) - 1) * kEmitWalkers] += 1u;
+                        m &= m - 1;
+                    }
+                }
                 if (o < p.cap) p.out[o] = pos0 + k;
                 ++o;
             }
@@ -287,15 +372,19 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             if (!(s_rescan[j] & 1)) continue;
             const uint64_t cj = (uint64_t)blockIdx.x * nthr + j;
             const unsigned long long oj = s_off[j];
-            if (oj >= p.cap) continue;
+            if (oj >= p.cap && !lab) continue;
             unsigned long long o = oj;
             const uint64_t b = cj * S;
             const uint64_t from = b > p.lo ? b : p.lo;
             const uint64_t to = b + S < p.hi ? b + S : p.hi;
             uint32_t q = cj ? p.last_state[cj - 1] : 0u;
-            for (uint64_t rs = b; rs < to && o < p.cap; rs += kTile) {
+            for (uint64_t rs = b; rs < to && (o < p.cap || lab); rs += kTile) {
                 uint32_t k0, k1;
                 row_span(rs, from, to, k0, k1);
+                // a whole row of bases: two symbols per lookup
+                if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile &&
+                    walk_row_pairs_lab(p, ptab, rs, q, o, false, s_wlab + tid))
+                    continue;
                 q = walk_row(slot, rs, k0, k1, q, o);
             }
         }
@@ -320,17 +409,27 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             }
             const uint64_t cj = (uint64_t)blockIdx.x * nthr + lo;
             unsigned long long o = s_off[lo] + rec[2];
-            if (o >= p.cap) continue;
+            if (o >= p.cap && !lab) continue;
             const uint64_t b = cj * S;
             const uint64_t cend = b + S < p.hi ? b + S : p.hi;
             const bool all_bases = (rec[0] & kRowAllBases) != 0;
             const uint64_t rs = b + (uint64_t)(rec[0] & ~kRowAllBases) * kTile;
             uint32_t k0, k1;
             row_span(rs, rs > p.lo ? rs : p.lo, rs + kTile < cend ? rs + kTile : cend, k0, k1);
+            uint32_t q_row = rec[1];
             if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile &&
-                walk_row_pairs(p, ptab, rs, rec[1], o, all_bases))
+                (lab ? walk_row_pairs_lab(p, ptab, rs, q_row, o, all_bases, s_wlab + tid)
+                     : walk_row_pairs(p, ptab, rs, rec[1], o, all_bases)))
                 continue;
             walk_row(slot, rs, k0, k1, rec[1], o);
+        }
+    }
+    if (lab) {
+        __syncthreads();
+        if (tid < p.n_labels) {
+            unsigned long long t = 0;
+            for (int w = 0; w < kEmitWalkers; ++w) t += s_wlab[tid * kEmitWalkers + w];
+            if (t) atomicAdd(&p.label_counts[tid], t);
         }
     }
 }
@@ -681,7 +780,8 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
 namespace dnalib {
 
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
-              uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov) {
+              uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
+              const LabelOut *lab) {
     if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
     const uint32_t req = ov ? ov->placement : 0u;
     if (req > DNA_PLACE_MAP) return DNA_ERR_INVALID_ARG;
@@ -696,14 +796,14 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
             record_launch();
             return cuda_status(cudaGetLastError());
         }
-        return map_scan_impl(d, seq, len, stream, out_count, out_positions, cap);
+        return map_scan_impl(d, seq, len, stream, out_count, out_positions, cap, nullptr, 0, lab);
     }
-    return scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, ov, nullptr);
+    return scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, ov, nullptr, lab);
 }
 
 int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                     uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
-                    const uint32_t *given_start) {
+                    const uint32_t *given_start, const LabelOut *lab) {
     if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
     if (len > (1ull << 40)) return DNA_ERR_INVALID_ARG;
     int cur_dev = -1;
@@ -717,7 +817,8 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;
     const uint64_t total = len + shift;
-    const bool positions = out_positions != nullptr && cap > 0;
+    const bool positions = (out_positions != nullptr && cap > 0) || lab != nullptr;
+    if (!out_positions) cap = 0;
     Plan pl;
     int rc = make_plan(d, total, positions, ov, pl);
     if (rc) return rc;
@@ -763,11 +864,16 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
         ep.spec_start = s.spec_start; ep.fix_delta = s.fix_delta;
         ep.flags = s.flags; ep.cta_off = s.cta_off; ep.out = out_positions; ep.cap = cap;
         ep.lut_lo = 0x00630061u; ep.lut_hi = 0x00670074u;
+        ep.labels = lab ? lab->labels : nullptr;
+        ep.label_counts = lab ? lab->counts : nullptr;
+        ep.pos_labels = lab ? lab->pos_labels : nullptr;
+        ep.n_labels = lab ? lab->n_labels : 0u;
         const uint32_t cpb = (uint32_t)pl.warps * 32u;   // one extraction thread per chunk
         const uint32_t tab5_smem = d->n_states * 5u <= 4096u ? 1u : 0u;
         const uint32_t ptab_smem = d->n_states <= 1024u ? 1u : 0u;   // 64 B per state
         const size_t esmem = (size_t)kEmitWalkers * kEmitRowPitch + (size_t)cpb * 16 + (size_t)(cpb + 1) * 4 +
-                             (tab5_smem ? (size_t)d->n_states * 20 : 0) + (ptab_smem ? (size_t)d->n_states * 64 : 0);
+                             (tab5_smem ? (size_t)d->n_states * 20 : 0) + (ptab_smem ? (size_t)d->n_states * 64 : 0) +
+                             (lab ? (size_t)32 * kEmitWalkers * 4 : 0);
         const size_t optin = device_props(d->device).smem_optin;
         // the extraction kernel's static shared memory is about 10 KB; 16 KB is reserved
         int rc2 = ensure_smem_optin((const void *)emit_kernel, d->device, (optin ? optin : 232448) - 16384);
@@ -893,11 +999,59 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
     return DNA_OK;
 }
 
+extern "C" int dfa_load_labeled(const uint32_t *table, uint32_t n_states, const uint32_t *labels,
+                                uint32_t n_labels, dna_dfa **out) {
+    if (!table || !labels || !out || n_states == 0 || n_states > kMaxStates || n_labels == 0 || n_labels > 32)
+        return DNA_ERR_INVALID_ARG;
+    const uint32_t allowed = n_labels == 32 ? 0xFFFFFFFFu : ((1u << n_labels) - 1u);
+    std::vector<uint8_t> mask((n_states + 7) / 8, 0);
+    for (uint32_t q = 0; q < n_states; ++q) {
+        if (labels[q] & ~allowed) return DNA_ERR_INVALID_ARG;
+        if (labels[q]) mask[q >> 3] |= (uint8_t)(1u << (q & 7));
+    }
+    dna_dfa *d = nullptr;
+    int rc = dfa_load(table, n_states, mask.data(), &d);
+    if (rc) return rc;
+    cudaError_t e = device_alloc((void **)&d->d_labels, sizeof(uint32_t) * n_states);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d->d_labels, labels, sizeof(uint32_t) * n_states, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dfa_free(d);
+        return cuda_status(e);
+    }
+    d->n_labels = n_labels;
+    *out = d;
+    return DNA_OK;
+}
+
 extern "C" void dfa_free(dna_dfa *d) {
     if (!d) return;
     cudaFree(d->d_one);
     cudaFree(d->d_pair);
+    cudaFree(d->d_labels);
     delete d;
+}
+
+extern "C" int dna_scan_labels(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t stream_h,
+                               uint64_t *out_count, uint64_t *out_label_counts, uint64_t *out_positions,
+                               uint32_t *out_pos_labels, uint64_t positions_capacity) {
+    if (!dfa || !out_count || !out_label_counts || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
+    if (!dfa->d_labels || dfa->n_labels == 0) return DNA_ERR_INVALID_ARG;
+    if (out_pos_labels && !out_positions) return DNA_ERR_INVALID_ARG;
+    if (len > (1ull << 40)) return DNA_ERR_INVALID_ARG;
+    int cur_dev = -1;
+    DNA_CUDA(cudaGetDevice(&cur_dev));
+    if (cur_dev != dfa->device) return DNA_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_h;
+    DNA_CUDA(cudaMemsetAsync(out_label_counts, 0, sizeof(uint64_t) * dfa->n_labels, stream));
+    if (len == 0) return scan_impl(dfa, seq, len, stream, out_count, nullptr, 0, nullptr);
+    LabelOut lab;
+    lab.labels = dfa->d_labels;
+    lab.counts = reinterpret_cast<unsigned long long *>(out_label_counts);
+    lab.pos_labels = out_positions ? out_pos_labels : nullptr;
+    lab.n_labels = dfa->n_labels;
+    return scan_impl(dfa, seq, len, stream, out_count, out_positions, out_positions ? positions_capacity : 0,
+                     nullptr, &lab);
 }
 
 extern "C" int dfa_info(const dna_dfa *d, dna_dfa_info *out) {
@@ -909,6 +1063,7 @@ extern "C" int dfa_info(const dna_dfa *d, dna_dfa_info *out) {
     out->accept_start = d->accept0;
     out->device = d->device;
     out->chunk_maps = d->map_mode ? 1u : 0u;
+    out->n_labels = d->n_labels;
     return DNA_OK;
 }
 

@@ -59,6 +59,29 @@ def test_host_compiler_matches_oracle_compiler(pattern):
     assert (_oracle_accept(m, t.shape[0]) == ao).all()
 
 
+@pytest.mark.parametrize("patterns", [
+    synth.REGEX_DNA_TABLE_V, ["TA", "AT"], ["CA", "A"], ["A{2}", "AA", "A"],
+    ["ACG[AT]{2,6}C(G|T)T", "TATAAA", "A(C|G)*T"], synth.random_regexes(71, 12), synth.random_regexes(72, 32)])
+def test_pattern_set_compiler_matches_oracle(patterns):
+    """One labelled automaton for several patterns: the library's (Glushkov positions of
+    the union, a mask per state from each pattern's last positions, Hopcroft from the
+    partition by mask) and the oracle's (Thompson NFA with an exit per pattern, subset
+    construction, Moore from the partition by mask) are identical in canonical numbering."""
+    t, lab = dna.compile_regex_set(patterns)
+    to, lo = oracle.compile_regex_set(patterns)
+    assert t.shape == to.shape and (t == to).all()
+    assert (lab == lo).all()
+
+
+def test_pattern_set_compiler_errors():
+    with pytest.raises(dna.DnaError):
+        dna.compile_regex_set(["A", "A*"])
+    with pytest.raises(dna.DnaError):
+        dna.compile_regex_set(["A("])
+    with pytest.raises(dna.DnaError):
+        dna.compile_regex_set(["A"] * 33)
+
+
 def test_kmer_compiler_matches_oracle():
     for seed in range(20):
         kmers = synth.random_kmers(seed, 1 + seed * 3, 4, 12)

@@ -293,3 +293,76 @@ def test_markov_generator_gc_fraction():
     seq = synth.markov2(1, 1 << 22)
     gc = np.isin(seq, np.frombuffer(b"CG", np.uint8)).mean()
     assert abs(gc - 0.41) < 0.002
+
+
+# ------------------------------------------------------- pattern labels (f3)
+
+LABEL_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "label_examples.tsv")
+
+
+def _label_rows():
+    rows = []
+    for line in open(LABEL_GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        pats, seq, pos, masks, counts, cite = line.rstrip("\n").split("\t")
+        rows.append((pats.split(";"), seq, [int(x) for x in pos.split(",")],
+                     [int(x) for x in masks.split(",")], [int(x) for x in counts.split(",")], cite))
+    return rows
+
+
+@pytest.mark.parametrize("row", _label_rows(), ids=lambda r: ";".join(r[0]) + ":" + r[1])
+def test_labelled_hand_worked_examples(row):
+    """Hand-worked positions, label masks and per-pattern counts (Alg. 1's counter per
+    accepting state), from the minimised and the raw labelled automaton."""
+    pats, seq, pos, masks, counts, _ = row
+    for minimise in (True, False):
+        t, lab = oracle.compile_regex_set(pats, minimise=minimise)
+        c, per, p, m = oracle.run_labels(t, lab, len(pats), seq.encode())
+        assert c == len(pos) and list(p) == pos and list(m) == masks and list(per) == counts
+
+
+def test_labelled_run_equals_separate_runs_and_brute_force():
+    """One automaton for the nine Table V expressions reports, for every expression, the
+    positions of that expression's own automaton run alone, and those of Python's re over
+    every window; a step counts once in the total however many expressions end there."""
+    pats = synth.REGEX_DNA_TABLE_V
+    t, lab = oracle.compile_regex_set(pats)
+    rng = np.random.default_rng(61)
+    for trial in range(3):
+        # a short random sequence with planted occurrences of Table V words
+        seq = bytearray(random_seq(rng, 3000))
+        for w in (b"AGGGTAAA", b"TTTACCCT", b"CGGGTAAA", b"AGGGTAAT", b"GTTACCCT", b"AAGGTAAA"):
+            at = int(rng.integers(0, len(seq) - len(w)))
+            seq[at:at + len(w)] = w
+        seq = bytes(seq)
+        c, per, pos, masks = oracle.run_labels(t, lab, len(pats), seq)
+        union = set()
+        for i, p in enumerate(pats):
+            alone = list(oracle.run(*oracle.compile_regex(p), seq)[1])
+            assert alone == re_window_positions(seq, p)
+            assert per[i] == len(alone)
+            assert [int(x) for x, m in zip(pos, masks) if m >> i & 1] == alone
+            union |= set(alone)
+        assert c == len(union) and list(pos) == sorted(union)
+        assert all(m != 0 for m in masks)
+    # the union of the labels is the alternation of the expressions compiled as one regex
+    seq = synth.markov2(62, 200_000).tobytes()
+    ta, aa = oracle.compile_regex("|".join(f"({p})" for p in pats))
+    assert oracle.run_labels(t, lab, len(pats), seq, positions=False)[0] == oracle.run(ta, aa, seq, positions=False)[0]
+
+
+def test_labelled_minimisation_keeps_labels_apart():
+    """Minimisation merges only states with equal masks: a set with a repeated pattern
+    keeps both counters, and each label's language is that of its own pattern."""
+    t, lab = oracle.compile_regex_set(["ACG[AT]{2,6}C(G|T)T", "ACG[AT]{2,6}C(G|T)T", "TATAAA"])
+    ts, as_ = oracle.compile_regex("TATAAA")
+    seq = synth.markov2(63, 300_000)
+    c, per, pos, masks = oracle.run_labels(t, lab, 3, seq)
+    assert per[0] == per[1]
+    assert per[2] == oracle.run(ts, as_, seq, positions=False)[0]
+    raw_t, raw_lab = oracle.compile_regex_set(["ACG[AT]{2,6}C(G|T)T", "ACG[AT]{2,6}C(G|T)T", "TATAAA"],
+                                               minimise=False)
+    assert raw_t.shape[0] >= t.shape[0]
+    c2, per2, pos2, masks2 = oracle.run_labels(raw_t, raw_lab, 3, seq)
+    assert c2 == c and list(per2) == list(per) and np.array_equal(pos2, pos) and np.array_equal(masks2, masks)
