@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MiB = 1 << 20
+PLACEMENTS = ["auto", "smem pair", "smem one-symbol", "global one-symbol", "chunk maps", "smem hot-state rows",
+              "smem one-symbol per lane"]
 METRIC = "sequence GB/s scanned (count + positions)"
 WORKLOAD = ("plain scan: 256 MiB order-2 Markov A/C/G/T (41% GC, seed 1), minimal DFA of "
             "ACG[AT]{2,6}C(G|T)T, exact count + all match positions")
@@ -566,7 +568,7 @@ def bench_plain_configs(dna, torch, stream, peak):
     kms = kernel_ms(fn, 5)
     out["large_3_2GiB_AC1000"] = {
         "bytes": n, "ms_per_step": ms, "gbs": n / (ms * 1e-3) / 1e9, "matches": int(cnt.item()),
-        "n_states": info.n_states, "placement": ["auto", "smem pair", "smem one-symbol", "global one-symbol"][info.placement],
+        "n_states": info.n_states, "placement": PLACEMENTS[info.placement],
         "kernel_ms": kms, "hbm_frac": n / (kms * 1e-3) / 1e9 / peak, "output": "count"}
     del d
     torch.cuda.empty_cache()

@@ -122,8 +122,38 @@ typedef struct {
  * dna_plan.placement. Larger automata whose runs never meet are scanned with speculation
  * and repair, which is exact but walks every chunk boundary in order. */
 #define DNA_PLACE_MAP        4
+/* Hot-state rows (automata of 91 .. 16383 states, too large for per-lane two-symbol
+ * tables): two-symbol rows for the states a walk on random DNA visits most, as many as
+ * fit in shared memory beside one-symbol rows of every state (16-bit entries); a lane
+ * whose 4 symbols meet a state without a two-symbol row redoes them with one-symbol steps.
+ * Measured slower than DNA_PLACE_SMEM_ONE on GB300; chosen only by a plan or by dfa_tune. */
+#define DNA_PLACE_SMEM_HOT   5
+/* One-symbol table copied once per lane in shared memory (512 B per state, so automata of
+ * up to about 375 states): every lane reads its own bank, so lookups never conflict.
+ * Measured slower than DNA_PLACE_SMEM_ONE on GB300 (the one-symbol scans are bound by the
+ * dependent lookup chain and instruction issue, not by bank conflicts); chosen only by a
+ * plan or by dfa_tune. */
+#define DNA_PLACE_SMEM_ONE_REP 6
 
 int dfa_info(const dna_dfa *dfa, dna_dfa_info *out);
+
+/*
+ * dfa_tune -- the autotuner of the table placement (the lookup stride and table form):
+ * times every placement the automaton fits in (two-symbol copies per lane; one shared
+ * one-symbol table; one-symbol copies per lane; hot-state two-symbol rows; the
+ * one-symbol table in L2) on the caller's sample with CUDA events, three count-only
+ * scans each, and makes the fastest the handle's default (dna_dfa_info.placement).
+ * The paper's Sec. III-B.1 motivates one uniform cost per symbol; which table form
+ * gives the lowest cost depends on the automaton and the hardware, so it is measured.
+ *   seq, len   device sample (a few MiB to a few hundred MiB of typical input).
+ *   out_placement  receives the chosen DNA_PLACE_* (DNA_PLACE_MAP for chunk-map
+ *                  automata, which have no table placement to choose).
+ *   out_ms     NULL, or receives the chosen placement's time per scan.
+ * Synchronises 'stream'. Do not run it while scans of the same handle are in flight on
+ * other streams. Errors: DNA_ERR_INVALID_ARG, DNA_ERR_CUDA, DNA_ERR_NOMEM.
+ */
+int dfa_tune(dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t stream,
+             uint32_t *out_placement, float *out_ms);
 
 /*
  * dfa_analyze -- host-only analysis of a table in the dfa_load layout (no GPU needed).
@@ -235,11 +265,13 @@ int dna_scan_count_static(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,
  *   lookback       symbols read before a chunk to speculate its start state
  *                  (1 = the paper's possible starting states from one symbol);
  *                  0 = automatic; at most 64.
- *   warps_per_cta  8, 16, 24 or 32; 0 = automatic.
+ *   warps_per_cta  8, 16, 24 or 32 (8 or 16 with DNA_PLACE_SMEM_HOT); 0 = automatic.
  *   placement      DNA_PLACE_*; 0 = automatic. A placement the automaton does not fit
  *                  in returns DNA_ERR_CAPACITY.
  *   prefetch_tiles how many 128-byte tiles ahead each lane prefetches its chunk into L2;
  *                  0 = automatic, 255 = no prefetch, at most 64 otherwise.
+ *   hot_rows       DNA_PLACE_SMEM_HOT only: use two-symbol rows for at most this many
+ *                  states (the most visited first); 0 = as many as fit.
  */
 typedef struct {
     uint32_t chunk_bytes;
@@ -247,6 +279,7 @@ typedef struct {
     uint32_t warps_per_cta;
     uint32_t placement;
     uint32_t prefetch_tiles;
+    uint32_t hot_rows;
 } dna_plan;
 
 int dna_scan_planned(const dna_dfa *dfa, const uint8_t *seq, uint64_t len,

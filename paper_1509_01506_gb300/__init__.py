@@ -19,12 +19,13 @@ _lock = threading.Lock()
 _lib = None
 
 DNA_OK = 0
-PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE, PLACE_MAP = 0, 1, 2, 3, 4
+PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE, PLACE_MAP, PLACE_SMEM_HOT, PLACE_SMEM_ONE_REP = \
+    0, 1, 2, 3, 4, 5, 6
 
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
     "dna_scan_count_static", "dna_scan_host", "dfa_load_labeled", "dna_scan_labels",
-    "dna_compile_regex_set",
+    "dna_compile_regex_set", "dfa_tune",
     "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
     "dna_server_create", "dna_server_submit", "dna_server_poll", "dna_server_drain",
     "dna_server_stats", "dna_server_now_ns", "dna_server_free", "dna_fasta_parse",
@@ -50,7 +51,7 @@ class _Info(ctypes.Structure):
 class _Plan(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint32), ("lookback", ctypes.c_uint32),
                 ("warps_per_cta", ctypes.c_uint32), ("placement", ctypes.c_uint32),
-                ("prefetch_tiles", ctypes.c_uint32)]
+                ("prefetch_tiles", ctypes.c_uint32), ("hot_rows", ctypes.c_uint32)]
 
 
 class _Profile(ctypes.Structure):
@@ -137,6 +138,8 @@ def lib():
         L.dna_scan_labels.restype = i32
         L.dna_compile_regex_set.argtypes = [p, u32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(u32)]
         L.dna_compile_regex_set.restype = i32
+        L.dfa_tune.argtypes = [p, p, u64, p, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_float)]
+        L.dfa_tune.restype = i32
         L.dna_batch_create.argtypes = [p, u32, p, p, u32, ctypes.POINTER(_BatchOpts), p, ctypes.POINTER(p)]
         L.dna_batch_create.restype = i32
         L.dna_batch_run.argtypes = [p, p, p]
@@ -343,6 +346,14 @@ class Dfa:
         return DfaInfo(i.n_states, i.definite_depth, i.lookback, i.placement,
                        bool(i.accept_start), i.device, bool(i.chunk_maps), i.n_labels)
 
+    def tune(self, seq, stream=None) -> tuple[int, float]:
+        """dfa_tune: times every table placement the automaton fits in on 'seq' (a CUDA
+        uint8 tensor) and makes the fastest the default. Returns (placement, ms)."""
+        pl, ms = ctypes.c_uint32(), ctypes.c_float()
+        _check(lib().dfa_tune(self.handle, seq.data_ptr(), seq.numel(), _stream_handle(stream),
+                              ctypes.byref(pl), ctypes.byref(ms)), "dfa_tune")
+        return pl.value, ms.value
+
     def free(self):
         if self._h:
             lib().dfa_free(self._h)
@@ -389,7 +400,7 @@ def scan(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None,
     if plan:
         pl = _Plan(plan.get("chunk_bytes", 0), plan.get("lookback", 0),
                    plan.get("warps_per_cta", 0), plan.get("placement", 0),
-                   plan.get("prefetch_tiles", 0))
+                   plan.get("prefetch_tiles", 0), plan.get("hot_rows", 0))
         rc = L.dna_scan_planned(dfa.handle, seq.data_ptr(), seq.numel(), sh,
                                 out_count.data_ptr(), pos_ptr, cap, ctypes.byref(pl))
     else:

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/dna_dfa.h"
 
@@ -25,9 +26,16 @@ struct dna_dfa {
     bool map_mode = false;        // scans use chunk maps (runs from different states do not meet)
     uint32_t *d_labels = nullptr; // [n_states] label mask of each state (dfa_load_labeled), or null
     uint32_t n_labels = 0;
+    // hot-state tables (automata too large for per-lane two-symbol tables): u16 two-symbol
+    // rows [n_states][16] and one-symbol rows [n_states][4]; the device numbering puts the
+    // states a random walk visits most first, perm[q] = device number of the caller's q
+    uint16_t *d_hot2 = nullptr;
+    uint16_t *d_hot1 = nullptr;
+    std::vector<uint32_t> perm;
+    double hot_cover = 0;         // visit share of the hot rows that fit (random walk)
     // resident blocks per SM of each scan kernel variant with this automaton's shared
     // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
-    std::atomic<int> per_sm[3][4][2] = {};
+    std::atomic<int> per_sm[5][4][2] = {};
 };
 
 namespace dnalib {

@@ -23,7 +23,19 @@ constexpr uint32_t kMaxLookback = 64;
 constexpr uint32_t kMaxStates = 1u << 24;
 constexpr uint32_t kDefaultPrefetch = 0;  // tiles of L2 prefetch ahead of the stage
 
-enum Mode { MODE_PAIR = 0, MODE_ONE_SMEM = 1, MODE_ONE_GLOBAL = 2 };
+enum Mode { MODE_PAIR = 0, MODE_ONE_SMEM = 1, MODE_ONE_GLOBAL = 2, MODE_HOT = 3, MODE_ONE_REP = 4 };
+
+// MODE_ONE_REP: one-symbol table copied once per lane (lane l's copy in bank l). A state's
+// row holds [code][lane] entries of 4 bytes, 512 B in all; an entry is the shared address
+// of the next state's row for the same lane (bits 2..6 lane, bits 9..17 row; bits 7..8
+// take the next code) | next state accepts (bit 0).
+constexpr uint32_t kRepRowBytes = 512;
+constexpr uint32_t kRepAddrMask = 0x3FE7Cu;
+
+// Hot-state mode: automata of up to kHotMaxStates states (14-bit state numbers in u16
+// entries); its kernels run kHotWarps warps per block.
+constexpr uint32_t kHotMaxStates = 16383;
+constexpr int kHotWarps = 16;
 
 
 struct ScanParams {
@@ -62,6 +74,10 @@ struct ScanParams {
     // lowercase letters selected by the codes (a, c at bytes 0, 2; t, g at bytes 4, 6),
     // passed at run time so that they stay in registers across the unrolled row loop
     uint32_t lut_lo, lut_hi;
+    // MODE_HOT: u16 two-symbol rows of the first hot_rows states and one-symbol rows of
+    // every state (read as 32-bit words)
+    const uint32_t *hot2, *hot1;
+    uint32_t hot_rows;
 };
 
 using ScanFn = void (*)(ScanParams);
@@ -71,6 +87,8 @@ using ScanFn = void (*)(ScanParams);
 ScanFn scan_fn_pair(int warps, bool pos);
 ScanFn scan_fn_one_smem(int warps, bool pos);
 ScanFn scan_fn_one_global(int warps, bool pos);
+ScanFn scan_fn_hot(int warps, bool pos);
+ScanFn scan_fn_one_rep(int warps, bool pos);
 
 }  // namespace dnalib
 
@@ -382,9 +400,10 @@ scan_kernel(ScanParams p) {
     // behind the first tile's copies
     const uint32_t n1 = p.n_states * 4u;
     const uint32_t nc = MODE == MODE_PAIR ? p.n_states * 16u : 0u;
+    uint32_t rep_base = 0;   // MODE_ONE_REP: shared address of the replicated table
     constexpr int kPre = 2048 / (WARPS * 32) > 0 ? 2048 / (WARPS * 32) : 1;
     uint32_t pre[kPre];
-    if constexpr (MODE != MODE_ONE_GLOBAL) {
+    if constexpr (MODE != MODE_ONE_GLOBAL && MODE != MODE_HOT) {
 #pragma unroll
         for (int r = 0; r < kPre; ++r) {
             const uint32_t i = threadIdx.x + (uint32_t)r * WARPS * 32;
@@ -399,8 +418,35 @@ scan_kernel(ScanParams p) {
     OneTable T;
     T.reset_entry = p.reset_entry;
     uint32_t pair_base = 0;
+    // MODE_HOT: shared addresses of the two-symbol rows (32 B per hot state) and of the
+    // one-symbol rows (8 B per state) that follow them
+    const uint32_t hot_p = smem_base + (uint32_t)WARPS * kStages * kStageBytes;
+    const uint32_t hot_o = hot_p + (p.hot_rows + 1u) * 32u;
     if constexpr (MODE == MODE_ONE_GLOBAL) {
         T.t = p.one;
+    } else if constexpr (MODE == MODE_HOT) {
+        // the one-symbol table of the per-byte paths (rows with resets, the join's
+        // repairs) stays in global memory, where it is L2 resident
+        T.t = p.one;
+        // two-symbol rows of the hot states plus the sentinel row: entries next x 4 +
+        // accepting steps, a next state without a row replaced by the sentinel; then the
+        // one-symbol rows of every state (next | accepts << 14)
+        const uint32_t h = p.hot_rows, n2w = (h + 1u) * 8u, n1w = p.n_states * 2u;
+        auto conv = [&](uint32_t e) {
+            const uint32_t nx = e & 0x3FFFu;
+            return (nx < h ? nx : h) * 4u + (e >> 14);
+        };
+        for (uint32_t i = threadIdx.x; i < n2w; i += WARPS * 32) {
+            uint32_t v;
+            if (i < h * 8u) {
+                const uint32_t e = p.hot2[i];
+                v = conv(e & 0xFFFFu) | (conv(e >> 16) << 16);
+            } else {
+                v = (h * 4u) | ((h * 4u) << 16);
+            }
+            one_s[i] = v;
+        }
+        for (uint32_t i = threadIdx.x; i < n1w; i += WARPS * 32) one_s[n2w + i] = p.hot1[i];
     } else {
         // one-symbol table, then (pair mode) the compact pair table right after it
         uint32_t *tabs = one_s;
@@ -412,6 +458,18 @@ scan_kernel(ScanParams p) {
         for (uint32_t i = threadIdx.x + (uint32_t)kPre * WARPS * 32; i < n1 + nc; i += WARPS * 32)
             tabs[i] = i < n1 ? p.one[i] : p.pair[i - n1];
         T.t = one_s;
+        if (MODE == MODE_ONE_REP) {
+            // every lane's copy of the one-symbol table, expanded from the compact copy
+            const uint32_t after = smem_base + (uint32_t)WARPS * kStages * kStageBytes + n1 * 4u;
+            rep_base = (after + 2047u) & ~2047u;
+            uint32_t *rep_ptr = reinterpret_cast<uint32_t *>(smem + (rep_base - smem_base));
+            __syncthreads();
+            const uint32_t nr = p.n_states * 128u;
+            for (uint32_t i = threadIdx.x; i < nr; i += WARPS * 32) {
+                const uint32_t e = one_s[i >> 5];
+                rep_ptr[i] = (rep_base + (e & 0x7FFFFFFFu) * kRepRowBytes + (i & 31u) * 4u) | (e >> 31);
+            }
+        }
         if (MODE == MODE_PAIR) {
             // every lane's copy of the pair table is expanded from the compact copy
             const uint32_t *cbuf = one_s + n1;
@@ -486,6 +544,77 @@ scan_kernel(ScanParams p) {
         if (t == 0) {
             head_s[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
             if (threadIdx.x == 0) p.block_head[blockIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        if (MODE == MODE_HOT) {
+            // Two symbols per lookup through the hot states' rows. Their entries hold
+            // next state x 4 + accepting steps in the pair; a next state without a row
+            // reads as the sentinel row hot_rows, whose entries point to itself. A lane
+            // whose word (4 symbols) met the sentinel redoes it exactly with four
+            // one-symbol lookups, in a branch the warp enters only when some lane needs it.
+            // The whole warp runs the loop (lanes without a full row of this chunk follow
+            // along and discard the result), so that the vote sees every lane. The row is
+            // walked as two halves of 16 words through the same code.
+            const bool go = live && full;
+            const uint32_t qs = q;
+            uint32_t err = 0, rc = 0, qq = q, base_seen = 0;
+            const uint32_t k32 = p.k5, k8 = p.k5 >> 2;
+            const uint32_t sentinel = p.hot_rows;
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const uint32_t x = w[k] & 0x06060606u;
+                    const uint32_t y = mad_lo(x, 65u, 0u);   // pair codes at bits 7..10 and 23..26
+                    const uint32_t b1 = hot_p + ((y >> 6) & 30u), b2 = hot_p + ((y >> 22) & 30u);
+                    const uint32_t e1 = lds_u16(mad_lo(min(qq, sentinel), k32, b1));
+                    const uint32_t e2 = lds_u16(mad_lo(e1 & 0xFFFCu, k8, b2));
+                    uint32_t nq = e2 >> 2, nrc = rc + (e1 & 3u) + (e2 & 3u);
+                    const uint32_t z = x | (x >> 4);
+                    const uint32_t bad = (__byte_perm(lut_lo, lut_hi, __byte_perm(z, 0, 0x0020)) ^ w[k]) & 0xDFDFDFDFu;
+                    err |= bad;
+                    // a zero byte of 'bad' is a base: rows without any (N runs) take no walk
+                    base_seen |= (bad - 0x01010101u) & ~bad & 0x80808080u;
+                    // only a lane whose row is still all bases needs the exact redo (the
+                    // others discard this row's walk and take the per-byte path)
+                    const bool cold = go && nq == sentinel && err == 0;
+                    if (__any_sync(0xFFFFFFFFu, cold)) {
+                        // lanes that need no redo read one shared word (no bank conflict)
+                        uint32_t st = cold ? qq : 0u, c = 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t ej = lds_u16(mad_lo(st, k8, hot_o) + (cold ? ((x >> (8 * j)) & 6u) : 0u));
+                            st = cold ? (ej & 0x3FFFu) : 0u;
+                            c += ej >> 14;
+                        }
+                        if (cold) { nq = st; nrc = rc + c; }
+                    }
+                    qq = nq;
+                    rc = nrc;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) w[k] = w[k + 16];
+            }
+            if (!live) continue;
+            if (go && err == 0) {
+                if (POS && rc) { row0rec |= t == 0; record_hit_row(stash, nrec, t | kRowAllBases, qs, cnt); }
+                cnt += rc;
+                q = qq;
+            } else if (go && base_seen == 0) {
+                // every byte of the row resets: the run ends in q0, and counts each byte
+                // when q0 accepts
+                const uint32_t add = (reset_e >> 31) * (uint32_t)kTile;
+                if (POS && add) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, cnt); }
+                cnt += add;
+                q = 0;
+            } else {
+                // reset bytes or a sequence edge in this row: byte by byte with the global
+                // one-symbol table (a reset byte takes no lookup); the row is in L2
+                const uint32_t before = cnt;
+                q = row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
+                                     row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
+                if (POS && cnt != before) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, before); }
+            }
+            continue;
         }
         if (!live) continue;
 
@@ -566,8 +695,33 @@ scan_kernel(ScanParams p) {
                 q = e & 0x7FFFFFFFu;
                 done = true;
             }
+            if (MODE == MODE_ONE_REP && full) {
+                // One lookup per byte in the lane's own copy (no bank conflict): the entry
+                // already is the next row's address; the byte's code enters at bits 7..8.
+                // A reset byte takes the lane's row of q0 (with q0's accept bit) instead.
+                const uint32_t reset_l = (rep_base + (uint32_t)lane * 4u) | (reset_e >> 31);
+                uint32_t e = rep_base + q * kRepRowBytes + (uint32_t)lane * 4u, rc = 0, err = 0;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const uint32_t x = w[k] & 0x06060606u;
+                    const uint32_t z = x | (x >> 4);
+                    const uint32_t bad = (__byte_perm(lut_lo, lut_hi, __byte_perm(z, 0, 0x0020)) ^ w[k]) & 0xDFDFDFDFu;
+                    err |= bad;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t off = (j == 0 ? (x << 6) : (x >> (8 * j - 6))) & 0x180u;
+                        const uint32_t a = lds_u32((e & kRepAddrMask) | off);
+                        e = (bad & (0xFFu << (8 * j))) ? reset_l : a;
+                        rc += e & 1u;
+                    }
+                }
+                if (POS && rc) { row0rec |= t == 0; record_hit_row(stash, nrec, t | (err ? 0u : kRowAllBases), qs, cnt); }
+                cnt += rc;
+                q = ((e & 0x3FE00u) - rep_base) / kRepRowBytes;
+                done = true;
+            }
             if (!done) {
-                q = (MODE != MODE_ONE_SMEM && full) ? row_bytes_reg(T, qs, w, cnt)
+                q = (MODE != MODE_ONE_SMEM && MODE != MODE_ONE_REP && full) ? row_bytes_reg(T, qs, w, cnt)
                          : row_bytes_global(T, qs, p.abase, row_off > p.lo ? row_off : p.lo,
                                             row_off + kTile < p.hi ? row_off + kTile : p.hi, p.hi, cnt);
                 if (POS && cnt != before) { row0rec |= t == 0; record_hit_row(stash, nrec, t, qs, before); }

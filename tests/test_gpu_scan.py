@@ -100,8 +100,39 @@ def test_plain_large_reduced_kmers():
 
 
 def test_regex_dna_table_v():
+    """The nine Table V expressions as one regex: 106 states, too many for per-lane
+    two-symbol tables, so per-lane one-symbol tables by default; every placement agrees."""
     seq = noisy_markov(7, 4 * MiB + 3)
-    check("regex", "|".join(synth.REGEX_DNA_TABLE_V), seq)
+    pat = "|".join(synth.REGEX_DNA_TABLE_V)
+    assert dna.Dfa.from_regex(pat).info().placement == dna.PLACE_SMEM_ONE
+    for plan in (None, dict(placement=2), dict(placement=3), dict(placement=5),
+                 dict(placement=6, warps_per_cta=16), dict(placement=6, warps_per_cta=8, chunk_bytes=128)):
+        check("regex", pat, seq, plan=plan)
+
+
+@pytest.mark.parametrize("n_kmers", [14, 30, 48])
+def test_per_lane_one_symbol_tables_up_to_their_limit(n_kmers):
+    """k-mer automata of about 100 to 350 states take per-lane one-symbol tables (the
+    largest with 8 warps); counts and positions equal the oracle's."""
+    kmers = synth.random_kmers(90 + n_kmers, n_kmers, 8)
+    seq = noisy_markov(91, 2 * MiB + 77)
+    check("kmers", kmers, seq, offset=2, plan=dict(placement=6))
+    check("kmers", kmers, seq, offset=2, plan=dict(placement=6, warps_per_cta=8))
+
+
+def test_autotuner_picks_a_measured_placement_and_results_stay_exact():
+    """dfa_tune times the placements the automaton fits in and makes the fastest the
+    default; the scans after it still equal the oracle's."""
+    seq = noisy_markov(92, 8 * MiB + 5)
+    for kind, pat in (("regex", synth.CONFIG2_REGEX), ("regex", "|".join(synth.REGEX_DNA_TABLE_V)),
+                      ("kmers", synth.random_kmers(93, 300, 10))):
+        dfa = dna.Dfa.from_regex(pat) if kind == "regex" else dna.Dfa.from_kmers(pat)
+        pl, ms = dfa.tune(to_device(seq))
+        assert pl in (1, 2, 3, 5, 6) and ms > 0 and dfa.info().placement == pl
+        t, a = oracle_tables(kind, pat)
+        want_c, want_p = oracle.run(t, a, seq)
+        c, p = gpu_run(dfa, to_device(seq, 1), capacity=want_c + 1)
+        assert c == want_c and np.array_equal(p, want_p)
 
 
 @pytest.mark.parametrize("pattern", synth.random_regexes(3, 12))
@@ -120,6 +151,11 @@ PLANS = [
     dict(chunk_bytes=384, lookback=1, warps_per_cta=8, placement=2),
     dict(chunk_bytes=640, lookback=5, warps_per_cta=32, placement=3),
     dict(chunk_bytes=4096, lookback=64, warps_per_cta=16, placement=2),
+    dict(chunk_bytes=2048, lookback=1, warps_per_cta=16, placement=5),
+    dict(chunk_bytes=256, lookback=7, warps_per_cta=8, placement=5, hot_rows=3),
+    dict(chunk_bytes=1280, lookback=1, warps_per_cta=16, placement=5, hot_rows=1),
+    dict(chunk_bytes=128, lookback=1, warps_per_cta=24, placement=6),
+    dict(chunk_bytes=1024, lookback=9, warps_per_cta=8, placement=6),
 ]
 
 
@@ -156,7 +192,7 @@ def test_all_reset_bytes_and_all_byte_values():
     check("regex", "TATA", lower)
 
 
-@pytest.mark.parametrize("placement", [2, 3])
+@pytest.mark.parametrize("placement", [2, 3, 5, (5, 2), 6])
 def test_one_symbol_rows_with_every_byte_value(placement):
     """The one-symbol loops take a reset byte's entry without branching: every byte value
     (bases of both cases, N, IUPAC codes, control and high bytes) mixed into rows of
@@ -168,10 +204,15 @@ def test_one_symbol_rows_with_every_byte_value(placement):
     seq[pick] = bases[rng.integers(0, 8, size=int(pick.sum()))]
     seq[200000:260000] = ord("N")
     seq[300000:400000] = np.frombuffer(b"acgt", np.uint8)[rng.integers(0, 4, size=100000)]
-    for kind, pat in (("regex", "A[CG]T"), ("kmers", synth.random_kmers(41, 200, 6, 9))):
+    extra = {}
+    if isinstance(placement, tuple):   # the hot-state rows with very few two-symbol rows
+        placement, extra = placement[0], dict(hot_rows=placement[1])
+    # per-lane one-symbol copies hold at most a few hundred states: a smaller k-mer set
+    kmers = synth.random_kmers(41, 40 if placement == 6 else 200, 6, 9)
+    for kind, pat in (("regex", "A[CG]T"), ("kmers", kmers)):
         for chunk in (128, 2048):
-            check(kind, pat, seq, offset=3, plan=dict(chunk_bytes=chunk, placement=placement))
-    check("regex", "TATA", np.full(70000, ord("N"), np.uint8), plan=dict(placement=placement))
+            check(kind, pat, seq, offset=3, plan=dict(chunk_bytes=chunk, placement=placement, **extra))
+    check("regex", "TATA", np.full(70000, ord("N"), np.uint8), plan=dict(placement=placement, **extra))
 
 
 def test_accepting_start_state_raw_table():
@@ -183,7 +224,9 @@ def test_accepting_start_state_raw_table():
     want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
     dfa = dna.Dfa(table, dna.pack_accept(acc))
     assert dfa.info().accept_start
-    for plan in (None, dict(chunk_bytes=128, placement=2), dict(chunk_bytes=256, placement=3)):
+    for plan in (None, dict(chunk_bytes=128, placement=2), dict(chunk_bytes=256, placement=3),
+                 dict(chunk_bytes=384, placement=5), dict(chunk_bytes=384, placement=5, hot_rows=1),
+                 dict(chunk_bytes=256, placement=6)):
         c, p = gpu_run(dfa, to_device(seq, 3), capacity=want_c + 1, plan=plan)
         assert c == want_c and np.array_equal(p, want_p)
 
@@ -209,7 +252,8 @@ def test_non_definite_automaton_repair_and_cascade():
         parts.append(np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, size=int(rng.integers(1, 30)))])
     seq = np.concatenate(parts)
     for plan in (dict(chunk_bytes=128, lookback=1), dict(chunk_bytes=256, lookback=4, placement=2),
-                 dict(chunk_bytes=128, lookback=1, placement=3), None):
+                 dict(chunk_bytes=128, lookback=1, placement=3), None,
+                 dict(chunk_bytes=256, placement=5, hot_rows=2), dict(chunk_bytes=128, placement=6)):
         check("regex", "A(C|G)*T", seq, plan=plan)
 
 
@@ -227,7 +271,9 @@ def test_random_permutation_like_tables():
         want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
         dfa = dna.Dfa(table, dna.pack_accept(acc))
         for plan in (None, dict(chunk_bytes=128, lookback=2, placement=1),
-                     dict(chunk_bytes=512, lookback=1, placement=3)):
+                     dict(chunk_bytes=512, lookback=1, placement=3),
+                     dict(chunk_bytes=256, placement=5, hot_rows=int(rng.integers(1, Q + 1))),
+                     dict(chunk_bytes=384, placement=6)):
             c, p = gpu_run(dfa, to_device(seq, trial % 16), capacity=want_c + 3, plan=plan)
             assert c == want_c and np.array_equal(p, want_p), (trial, plan)
 
@@ -328,8 +374,20 @@ def test_dense_matches_overflow_stash():
 def test_large_aho_corasick_placements():
     seq = noisy_markov(6, 4 * MiB + 1)
     kmers = synth.random_kmers(6, 1000, 12)
-    for plan in (None, dict(placement=2), dict(placement=3), dict(placement=3, lookback=1)):
+    for plan in (None, dict(placement=2), dict(placement=3), dict(placement=3, lookback=1),
+                 dict(placement=5), dict(placement=5, hot_rows=64), dict(placement=5, hot_rows=1000),
+                 dict(placement=5, warps_per_cta=8), dict(placement=5, chunk_bytes=128)):
         check("kmers", kmers, seq, plan=plan, positions=True)
+
+
+def test_hot_state_rows_on_the_large_aho_corasick_automaton():
+    """Hot-state rows on the 1,000 12-mers of the 3.2 GiB workload (7,366 states, about
+    3,000 two-symbol rows, many lanes taking the one-symbol redo), on soft-masked
+    sequence with N runs: results equal the oracle's, counts and positions."""
+    kmers = synth.random_kmers(2, 1000, 12)
+    seq = noisy_markov(16, 16 * MiB + 3, n_frac=0.02, lower_frac=0.1)
+    for plan in (dict(placement=5), dict(placement=5, warps_per_cta=8)):
+        check("kmers", kmers, seq, offset=1, plan=plan)
 
 
 def test_invalid_arguments_are_rejected():
