@@ -109,6 +109,7 @@ void prof_end(ProfToken t, cudaStream_t s, int which);
 // host and summed when profiling is enabled.
 void prof_conv(cudaStream_t s, const uint32_t *dev_ctrl, uint64_t nseg);
 void profile_set(int on);
+bool profiling();
 void profile_collect(dna_profile_t *out, int reset);
 
 }  // namespace dnalib

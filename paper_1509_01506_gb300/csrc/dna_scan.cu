@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
     // everything above reads only the automaton; the scan's results are read below, after
     // the scan grid has completed (a no-op when not launched as a programmatic dependent)
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the next scan on the stream may start its prologue now (it waits for this grid
+    // before it touches memory this grid uses)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint64_t c = (uint64_t)blockIdx.x * nthr + tid;
     const bool act = c < p.nseg;
     const unsigned long long v = act ? p.count[c] : 0u;
@@ -528,6 +531,29 @@ int scratch_alloc(int dev, size_t bytes, cudaStream_t s, void **out) {
     return DNA_OK;
 }
 
+// Control words of the chunk scan that stay with a stream: zeroed once when first used,
+// and left zero by every scan's last block, so a scan needs no memset before it. Kept for
+// the life of the process (32 bytes per device and stream, at most kStreamCtrlMax).
+static std::mutex g_sctrl_mu;
+struct StreamCtrl { int dev; cudaStream_t s; uint32_t *ctrl; };
+static std::vector<StreamCtrl> g_sctrl;
+constexpr size_t kStreamCtrlMax = 1024;
+
+uint32_t *stream_ctrl(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_sctrl_mu);
+    for (const StreamCtrl &c : g_sctrl)
+        if (c.dev == dev && c.s == s) return c.ctrl;
+    if (g_sctrl.size() >= kStreamCtrlMax) return nullptr;
+    // not while the stream is being captured into a graph (no allocation there)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    uint32_t *c = nullptr;
+    if (device_alloc((void **)&c, 32) != cudaSuccess) return nullptr;
+    if (cudaMemset(c, 0, 32) != cudaSuccess) { cudaFree(c); return nullptr; }
+    g_sctrl.push_back({dev, s, c});
+    return c;
+}
+
 int scratch_free(void *p, cudaStream_t s) {
     if (!p) return DNA_OK;
     return cuda_status(cudaFreeAsync(p, s));
@@ -594,6 +620,7 @@ void prof_conv(cudaStream_t s, const uint32_t *dev_ctrl, uint64_t nseg) {
 }
 
 void profile_set(int on) { g_profile.store(on ? 1 : 0); }
+bool profiling() { return g_profile.load(std::memory_order_relaxed) != 0; }
 
 void profile_collect(dna_profile_t *out, int reset) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -864,7 +891,11 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     rc = scratch_alloc(d->device, s.bytes, stream, &mem);
     if (rc) return rc;
     carve(s, pl.nseg, nblocks, positions, pending_cap, div_cap, (uint8_t *)mem);
-    cudaError_t e = cudaMemsetAsync(s.ctrl, 0, 32, stream);
+    // the stream's own control words (already zero) unless profiling reads them back
+    uint32_t *sctrl = profiling() ? nullptr : stream_ctrl(d->device, stream);
+    cudaError_t e = cudaSuccess;
+    if (sctrl) s.ctrl = sctrl;
+    else e = cudaMemsetAsync(s.ctrl, 0, 32, stream);
 
     ScanParams sp;
     sp.abase = abase; sp.lo = shift; sp.hi = total; sp.seg_bytes = pl.seg_bytes; sp.nseg = pl.nseg;
@@ -874,6 +905,7 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     sp.stash = s.stash; sp.nrec = s.nrec; sp.flags = s.flags; sp.fix_delta = s.fix_delta;
     sp.prefetch_tiles = pl.prefetch;
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
+    sp.reset_ctrl = sctrl ? 1u : 0u;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
     sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
     sp.k1 = 1u; sp.k5 = 1u << 5;
@@ -884,8 +916,22 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
 
     const ProfToken tok = e == cudaSuccess ? prof_begin(stream) : ProfToken{};
     if (e == cudaSuccess) {
-        scan_fn(pl.mode, pl.warps, pl.pos)<<<pl.grid, pl.warps * 32, pl.smem, stream>>>(sp);
-        e = cudaGetLastError();
+        // programmatic dependent launch: the scan's prologue (tables into shared memory,
+        // the first tile's copies) overlaps the end of the kernel before it on the stream;
+        // the kernel waits (griddepcontrol.wait) before touching anything that kernel may
+        // write. Profiling serialises it (events sit between the kernels).
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)pl.grid);
+        cfg.blockDim = dim3((unsigned)(pl.warps * 32));
+        cfg.dynamicSmemBytes = pl.smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = tok.a ? 0 : 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, scan_fn(pl.mode, pl.warps, pl.pos), sp);
+        if (e == cudaSuccess) e = cudaGetLastError();
         record_launch();
     }
     prof_end(tok, stream, PROF_SCAN);
@@ -1365,6 +1411,7 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     sp.stash = nullptr; sp.nrec = nullptr; sp.flags = s.flags; sp.fix_delta = nullptr;
     sp.prefetch_tiles = pl.prefetch;
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
+    sp.reset_ctrl = 0u;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
     sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
     sp.k1 = 1u; sp.k5 = 1u << 5;

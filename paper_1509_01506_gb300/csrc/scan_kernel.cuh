@@ -57,9 +57,11 @@ struct ScanParams {
     uint32_t *nrec;         // [nseg] hit rows recorded (may exceed kStashCap)
     uint8_t *flags;         // [nseg] kFlag* bits for the extraction pass
     uint32_t *fix_delta;    // [nseg] count offset shift of a kFlagFixed chunk's later rows
-    uint32_t *ctrl;         // [8] zeroed before launch: finish ticket, pending, diverged, then
+    uint32_t *ctrl;         // [8] zero at launch: finish ticket, pending, diverged, then
                             //   counters: chunks repaired in-block at the converging point,
                             //   block-first chunks joined with a wrong start, cascade walks
+    uint32_t reset_ctrl;    // 1: the last block zeroes ctrl[0..5] when it is done with them
+                            //   (a control block that stays with the stream between scans)
     uint32_t *pending;      // chunks whose 16-byte in-block repair did not converge (the last
     uint32_t pending_cap;   //   block repairs them; it joins every block's first chunk anyway)
     uint32_t *div_list;     // [div_cap] chunks whose last state changed in a repair
@@ -330,7 +332,13 @@ __device__ void finalize_block(const ScanParams &p, const OneTable &T, unsigned 
         if (tid == THREADS - 1) carry = incl;
         __syncthreads();
     }
-    if (tid == 0) *p.out_count = carry;
+    if (tid == 0) {
+        *p.out_count = carry;
+        // every other block took its ticket before this one, after its last use of the
+        // control words: leave them zero for the next scan on this stream
+        if (p.reset_ctrl)
+            for (int i = 0; i < 6; ++i) p.ctrl[i] = 0;
+    }
 }
 
 template <int MODE, int WARPS, bool POS>
@@ -486,6 +494,13 @@ scan_kernel(ScanParams p) {
         }
     }
     __syncthreads();
+    // Launched as a programmatic dependent of the kernel before it on the stream, this
+    // grid may start while that kernel finishes: everything above reads only the
+    // automaton's tables and the sequence. Anything a kernel before it may write or still
+    // read (the chunk start states of the chunk-map path, this call's scratch, which the
+    // memory pool may hand over from an earlier call, the output) is touched only after
+    // the wait. Without a programmatic predecessor the wait returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     uint32_t *stash = POS ? p.stash + seg * (kStashCap * 3) : nullptr;
     uint32_t nrec = 0;
     bool row0rec = false;   // the chunk's row 0 has a hit-row record
@@ -795,7 +810,7 @@ scan_kernel(ScanParams p) {
         if (k < p.pending_cap) p.pending[k] = (uint32_t)seg;
     }
     {   // convergence statistics: chunks whose speculated start was repaired in-block
-        // (added up in shared memory; one global add per block after its ticket)
+        // (added up in shared memory; one global add per block before its ticket)
         const uint32_t nfix = __popc(__ballot_sync(0xFFFFFFFFu, fixed));
         if (lane == 0 && nfix) atomicAdd(&s_nfix, nfix);
     }
@@ -814,9 +829,9 @@ scan_kernel(ScanParams p) {
         unsigned long long t = 0;
         for (int i = 0; i < WARPS; ++i) t += red[i];
         p.cta_sum[blockIdx.x] = t;
+        if (s_nfix) atomicAdd(&p.ctrl[3], s_nfix);
         __threadfence();
         is_last = atomicAdd(&p.ctrl[0], 1u) == gridDim.x - 1;
-        if (s_nfix) atomicAdd(&p.ctrl[3], s_nfix);
     }
     __syncthreads();
     if (!is_last) return;

@@ -451,3 +451,32 @@ def test_plain_large_full_size_count():
     del seq
     c, _ = gpu_run(dfa, dseq, positions=False)
     assert c == want_c
+
+
+def test_back_to_back_scans_on_two_streams_share_nothing_stale():
+    """Scans queued back to back on one stream reuse the stream's control words (left
+    zero by each scan); interleaving automata of every kind, with and without positions,
+    and a second stream gives each scan the oracle's result."""
+    seq = noisy_markov(95, 6 * MiB + 13)
+    table, acc = _permutation_automaton(6, 96)
+    auts = [("regex", synth.CONFIG2_REGEX, dna.Dfa.from_regex(synth.CONFIG2_REGEX)),
+            ("kmers", synth.random_kmers(97, 400, 11), None),
+            ("perm", None, dna.Dfa(table, dna.pack_accept(acc)))]
+    auts[1] = ("kmers", auts[1][1], dna.Dfa.from_kmers(auts[1][1]))
+    want = []
+    for kind, pat, _ in auts:
+        t, a = (table.astype(np.int32), acc) if kind == "perm" else oracle_tables(kind, pat)
+        want.append(oracle.run(t, a, seq))
+    d = to_device(seq, 4)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for r in range(3):
+        for k, (_, _, dfa) in enumerate(auts):
+            st = s1 if (r + k) % 2 == 0 else s2
+            c, p = dna.scan(dfa, d, positions=(r != 1), capacity=want[k][0] + 1, stream=st)
+            outs.append((k, r != 1, c, p))
+    torch.cuda.synchronize()
+    for k, pos, c, p in outs:
+        assert int(c.item()) == want[k][0]
+        if pos:
+            assert np.array_equal(p[:want[k][0]].cpu().numpy(), want[k][1])
