@@ -334,11 +334,19 @@ def bench_batched(args, dna, torch, stream, clocks_mhz):
         "total_matches": int(counts.sum()),
         "cpu_baseline": cpu_batched,
     }
-    peak = lds_lookup_peak(torch.cuda.get_device_properties(0).multi_processor_count, clocks_mhz or 2070.0)
-    lookups = total * info.n_fast * 0.5    # one two-symbol lookup per 2 bases per automaton
-    res["roofline"] = {"bound": "alu", "unit": "lookups/s", "achieved": lookups / (k_ms * 1e-3),
-                       "peak": peak, "frac": lookups / (k_ms * 1e-3) / peak,
-                       "peak_source": "SMs x 32 shared-memory lookups per clock x SM clock (median under load)"}
+    # the method's unit: one transition per base per automaton; the kernel takes them two at
+    # a time (one two-symbol lookup per 2 bases per automaton, each lane in its own bank),
+    # so its peak is twice the measured conflict-free lookup rate
+    peak_lk = dna.lookup_peak(0, stream=stream)
+    transitions = total * info.n_fast
+    res["roofline"] = {"bound": "alu", "unit": "transitions/s", "achieved": transitions / (k_ms * 1e-3),
+                       "peak": 2 * peak_lk, "frac": transitions / (k_ms * 1e-3) / (2 * peak_lk),
+                       "lookups_per_s": transitions * 0.5 / (k_ms * 1e-3), "lookup_peak": peak_lk,
+                       "peak_source": "dna_lookup_peak mode 0 (measured: shared-memory lookups with no bank "
+                                      "conflict, 8 chains per thread, one full block per SM) x 2 transitions "
+                                      "per two-symbol lookup",
+                       "derived_peak_for_context": lds_lookup_peak(
+                           torch.cuda.get_device_properties(0).multi_processor_count, clocks_mhz or 2070.0)}
     if not args.no_percall:
         # the same pairs, one dna_scan (count only) per (sequence, automaton)
         cnt = torch.empty((n_s, len(dfas)), dtype=torch.int64, device="cuda")
@@ -374,51 +382,25 @@ SERVE_WORKLOAD = ("serving: Poisson arrivals at 2,000 req/s (seed 4), lengths lo
                   "regexes); 8 slots, 40 GiB admission cap")
 
 
-def serve_automata(dna):
-    """16 automata: 8 k-mer sets (random 8..16-mers, as many as keep <= 500 states) and
-    8 motif regexes."""
-    import synth
+def serve_automata(dna, patterns):
+    """The 16 resident automata of the serving workload (synth.serving's pattern sets)."""
     dfas, kinds = [], []
-    for i in range(8):
-        n = 40
-        while True:
-            km = synth.random_kmers(400 + i, n, 8, 16)
-            q = dna.compile_kmers(km)[0].shape[0]
-            if q <= 500 or n <= 4:
-                break
-            n -= 4
-        dfas.append(dna.Dfa.from_kmers(km))
-        kinds.append(("kmers", n, q))
-    for r in synth.random_regexes(4, 8):
-        d = dna.Dfa.from_regex(r)
+    for kind, pat in patterns:
+        d = dna.Dfa.from_kmers(pat) if kind == "kmers" else dna.Dfa.from_regex(pat)
         dfas.append(d)
-        kinds.append(("regex", r, d.info().n_states))
+        kinds.append((kind, len(pat) if kind == "kmers" else pat, d.info().n_states))
     return dfas, kinds
 
 
-def bench_serve(args, dna, torch):
-    import synth
-    n_pay = 256 * MiB
-    payload = synth.markov2(4, n_pay)
-    synth.overlay_runs(payload, 4, 0.10, 1000.0, "lower")
-    synth.overlay_runs(payload, 5, 0.02, 50000.0, "N")
-    pinned = torch.from_numpy(payload).pin_memory()
-    dfas, kinds = serve_automata(dna)
-    n_req = args.serve_requests
-    rng = np.random.Generator(np.random.PCG64(4))
-    lens = synth.log_uniform_lengths(4, n_req, 4 * 1024, 64 * MiB)
-    offs = np.array([int(rng.integers(0, n_pay - n + 1)) for n in lens], np.int64)
-    didx = rng.integers(0, len(dfas), n_req)
-    gaps = rng.exponential(1e9 / 2000.0, n_req)
-    srv = dna.Server(dfas, slots=8, mem_cap_bytes=40 << 30)
-    base = pinned.data_ptr()
-    # warm the slots (first-call set-up of each kernel variant), then the timed schedule
-    for i in range(16):
+def run_served(dna, dfas, base, lens, offs, didx, arrivals, slots=8):
+    """Submits every request (host slices of the pinned payload at 'base') with its
+    arrival time and drains; returns the completions in request order."""
+    n_req = len(lens)
+    srv = dna.Server(dfas, slots=slots, mem_cap_bytes=40 << 30)
+    for i in range(16):   # first-call set-up of each kernel variant on the slots
         srv.submit((base, 1 << 20), i % len(dfas))
     srv.drain()
     srv.poll(64)
-    t0 = dna.Server.now_ns() + 50_000_000
-    arrivals = (t0 + np.cumsum(gaps)).astype(np.int64)
     ids = {}
     for i in range(n_req):
         ids[srv.submit((base + int(offs[i]), int(lens[i])), int(didx[i]), int(arrivals[i]))] = i
@@ -429,37 +411,87 @@ def bench_serve(args, dna, torch):
     res = [None] * n_req
     for c in comps:
         res[ids[c["id"]]] = c
+    return res
+
+
+def serve_stats(res, lens):
     lat = np.array([(c["done_ns"] - c["arrival_ns"]) / 1e6 for c in res])
     lat_noh2d = np.array([(c["done_ns"] - c["arrival_ns"]) / 1e6 - c["h2d_us"] / 1e3 for c in res])
     dev = np.array([c["device_us"] / 1e3 for c in res])
     span_s = (max(c["done_ns"] for c in res) - min(c["arrival_ns"] for c in res)) / 1e9
-    total = int(lens.sum())
-    # every count against one dna_scan of the same slice on the device
-    dpay = pinned.cuda()
-    out = torch.empty(n_req, dtype=torch.int64, device="cuda")
-    sh = int(torch.cuda.current_stream().cuda_stream)
-    for i in range(n_req):
-        dna.scan_ptr(dfas[int(didx[i])], dpay.data_ptr() + int(offs[i]), int(lens[i]), out.data_ptr() + 8 * i, sh)
-    torch.cuda.synchronize()
-    same = bool(np.array_equal(out.cpu().numpy(), np.array([c["count"] for c in res], np.int64)))
-    ok = all(c["status"] == 0 for c in res)
     ev = sorted([(c["admit_ns"], 1) for c in res] + [(c["done_ns"], -1) for c in res])
     conc = peak = 0
     for _, d in ev:
         conc += d
         peak = max(peak, conc)
-    del dpay
-    return {
-        "workload": SERVE_WORKLOAD, "requests": n_req, "bytes": total,
-        "offered_gbs": total / (float(gaps.sum()) / 1e9) / 1e9,
-        "gbs": total / span_s / 1e9, "span_s": span_s,
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "p50_ms_without_h2d": float(np.percentile(lat_noh2d, 50)),
-        "p99_ms_without_h2d": float(np.percentile(lat_noh2d, 99)),
-        "device_p50_ms": float(np.percentile(dev, 50)), "device_p99_ms": float(np.percentile(dev, 99)),
-        "max_concurrent": peak, "all_ok": ok, "identical_to_single_calls": same,
-        "automata_states": [k[2] for k in kinds],
-    }
+    return {"gbs": int(lens.sum()) / span_s / 1e9, "span_s": span_s,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_without_h2d": float(np.percentile(lat_noh2d, 50)),
+            "p99_ms_without_h2d": float(np.percentile(lat_noh2d, 99)),
+            "device_p50_ms": float(np.percentile(dev, 50)), "device_p99_ms": float(np.percentile(dev, 99)),
+            "max_concurrent": peak, "all_ok": all(c["status"] == 0 for c in res)}
+
+
+def bench_serve(args, dna, torch):
+    """The serving workload at its Poisson rate (2,000 req/s), then overloaded (every
+    request queued at once: the loop's capacity), then the same requests one at a time
+    through dna_scan_host (the per-call path); counts must agree across all three and
+    with one dna_scan of each slice. (A seeded sample of these requests, 64 MiB ones and
+    every automaton included, is checked against the oracle by
+    tests/test_gpu_serve.py::test_bench_serving_sample_equals_the_oracle.)"""
+    import synth
+    w = synth.serving(n_req=args.serve_requests, n_states=lambda km: dna.compile_kmers(km)[0].shape[0])
+    pinned = torch.from_numpy(w["payload"]).pin_memory()
+    dfas, kinds = serve_automata(dna, w["patterns"])
+    lens, offs, didx, gaps = w["lens"], w["offs"], w["didx"], w["gaps_ns"]
+    n_req = len(lens)
+    total = int(lens.sum())
+    base = pinned.data_ptr()
+    t0 = dna.Server.now_ns() + 50_000_000
+    poisson = run_served(dna, dfas, base, lens, offs, didx, (t0 + np.cumsum(gaps)).astype(np.int64))
+    t1 = dna.Server.now_ns() + 20_000_000
+    overload = run_served(dna, dfas, base, lens, offs, didx, np.full(n_req, t1, np.int64))
+    # the per-call path: the same requests one after another through dna_scan_host
+    stream = torch.cuda.current_stream()
+    cnt = np.zeros(1, np.uint64)
+    payload = w["payload"]
+    for i in range(8):
+        dna.scan_host(dfas[int(didx[i])], pinned[int(offs[i]):int(offs[i]) + int(lens[i])], stream=stream,
+                      out_count=cnt)
+    serial_counts = np.empty(n_req, np.int64)
+    s0 = time.perf_counter()
+    for i in range(n_req):
+        c, _ = dna.scan_host(dfas[int(didx[i])], pinned[int(offs[i]):int(offs[i]) + int(lens[i])],
+                             stream=stream, out_count=cnt)
+        serial_counts[i] = c
+    serial_s = time.perf_counter() - s0
+    # every count against one dna_scan of the same slice on the device
+    dpay = pinned.cuda()
+    out = torch.empty(n_req, dtype=torch.int64, device="cuda")
+    sh = int(stream.cuda_stream)
+    for i in range(n_req):
+        dna.scan_ptr(dfas[int(didx[i])], dpay.data_ptr() + int(offs[i]), int(lens[i]), out.data_ptr() + 8 * i, sh)
+    torch.cuda.synchronize()
+    single = out.cpu().numpy()
+    del dpay, payload
+    pc = np.array([c["count"] for c in poisson], np.int64)
+    oc = np.array([c["count"] for c in overload], np.int64)
+    p_stats, o_stats = serve_stats(poisson, lens), serve_stats(overload, lens)
+    res = {"workload": SERVE_WORKLOAD, "requests": n_req, "bytes": total,
+           "offered_gbs": total / (float(gaps.sum()) / 1e9) / 1e9}
+    res.update(p_stats)
+    res["capacity"] = {"gbs": o_stats["gbs"], "span_s": o_stats["span_s"], "all_ok": o_stats["all_ok"],
+                       "max_concurrent": o_stats["max_concurrent"],
+                       "p50_ms": o_stats["p50_ms"], "p99_ms": o_stats["p99_ms"],
+                       "note": "every request queued at once; latencies include the queueing"}
+    res["serial"] = {"gbs": total / serial_s / 1e9, "s": serial_s,
+                     "api": "dna_scan_host, one request after another (pinned host slices)"}
+    res["served_over_serial"] = o_stats["gbs"] / (total / serial_s / 1e9)
+    res["identical_to_single_calls"] = bool(np.array_equal(pc, single) and np.array_equal(oc, single)
+                                            and np.array_equal(serial_counts, single))
+    res["automata_states"] = [k[2] for k in kinds]
+    res["oracle_checked_by"] = "tests/test_gpu_serve.py::test_bench_serving_sample_equals_the_oracle"
+    return res
 
 
 
@@ -567,10 +599,24 @@ def bench_plain_configs(dna, torch, stream, peak):
     fn = lambda: dna.scan(dfa, d, stream=stream, out_count=cnt)
     ms = timed(fn, 10)
     kms = kernel_ms(fn, 5)
+    # the same scan with the one-symbol table in L2 (the placement of automata too large for
+    # shared memory), and the measured lookup peaks each placement is bound by
+    fn_g = lambda: dna.scan(dfa, d, stream=stream, out_count=cnt, plan=dict(placement=3))
+    kms_g = kernel_ms(fn_g, 3)
+    lk_smem, lk_l2 = dna.lookup_peak(1, stream=stream), dna.lookup_peak(2, stream=stream)
     out["large_3_2GiB_AC1000"] = {
         "bytes": n, "ms_per_step": ms, "gbs": n / (ms * 1e-3) / 1e9, "matches": int(cnt.item()),
         "n_states": info.n_states, "placement": PLACEMENTS[info.placement],
-        "kernel_ms": kms, "hbm_frac": n / (kms * 1e-3) / 1e9 / peak, "output": "count"}
+        "kernel_ms": kms, "hbm_frac": n / (kms * 1e-3) / 1e9 / peak, "output": "count",
+        "lookup_roofline": {"unit": "lookups/s", "achieved": n / (kms * 1e-3), "peak": lk_smem,
+                            "frac": n / (kms * 1e-3) / lk_smem,
+                            "peak_source": "dna_lookup_peak mode 1 (measured: shared-memory lookups at random "
+                                           "banks)"},
+        "global_placement": {"kernel_ms": kms_g, "gbs": n / (kms_g * 1e-3) / 1e9,
+                             "lookups_per_s": n / (kms_g * 1e-3), "gather_peak": lk_l2,
+                             "frac_of_gather_peak": n / (kms_g * 1e-3) / lk_l2,
+                             "peak_source": "dna_lookup_peak mode 2 (measured: random 4-byte gathers from a "
+                                            "128 KiB global table through L1/L2)"}}
     del d
     torch.cuda.empty_cache()
     return out

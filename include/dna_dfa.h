@@ -523,6 +523,20 @@ typedef struct {
 void dna_profile_enable(int enable);
 int  dna_profile_read(dna_profile_t *out, int reset);
 
+/*
+ * dna_lookup_peak -- measures the lookup throughput that bounds the scans (a measurement
+ * hook for their rooflines; the paper has no counterpart). Every thread of one full
+ * block per SM runs 8 chains of dependent 4-byte table lookups; the best of three timed
+ * runs (CUDA events on 'stream', after a warm-up run) gives lookups per second:
+ *   mode 0  shared memory, lane l reading only bank l (the per-lane table copies of the
+ *           two-symbol and chunk-map kernels): no bank conflict;
+ *   mode 1  shared memory, random entries of a 64 KiB table (the shared one-symbol table);
+ *   mode 2  global memory, random entries of a 128 KiB table read with ordinary (L1
+ *           cached) loads (the one-symbol table of automata too large for shared memory).
+ * Synchronises 'stream'. Errors: DNA_ERR_INVALID_ARG, DNA_ERR_CUDA, DNA_ERR_NOMEM.
+ */
+int dna_lookup_peak(uint32_t mode, dna_stream_t stream, double *lookups_per_s);
+
 #ifdef __cplusplus
 }
 #endif

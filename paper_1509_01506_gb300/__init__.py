@@ -25,7 +25,7 @@ PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE, PLACE_MAP, PLACE_
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
     "dna_scan_count_static", "dna_scan_host", "dfa_load_labeled", "dna_scan_labels",
-    "dna_compile_regex_set", "dfa_tune",
+    "dna_compile_regex_set", "dfa_tune", "dna_lookup_peak",
     "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
     "dna_server_create", "dna_server_submit", "dna_server_poll", "dna_server_drain",
     "dna_server_stats", "dna_server_now_ns", "dna_server_free", "dna_fasta_parse",
@@ -140,6 +140,8 @@ def lib():
         L.dna_compile_regex_set.restype = i32
         L.dfa_tune.argtypes = [p, p, u64, p, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_float)]
         L.dfa_tune.restype = i32
+        L.dna_lookup_peak.argtypes = [u32, p, ctypes.POINTER(ctypes.c_double)]
+        L.dna_lookup_peak.restype = i32
         L.dna_batch_create.argtypes = [p, u32, p, p, u32, ctypes.POINTER(_BatchOpts), p, ctypes.POINTER(p)]
         L.dna_batch_create.restype = i32
         L.dna_batch_run.argtypes = [p, p, p]
@@ -648,6 +650,14 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+def lookup_peak(mode: int, stream=None) -> float:
+    """dna_lookup_peak: measured lookups per second (0: shared memory without bank
+    conflicts, 1: shared memory at random banks, 2: random L2 gathers)."""
+    v = ctypes.c_double()
+    _check(lib().dna_lookup_peak(mode, _stream_handle(stream), ctypes.byref(v)), "dna_lookup_peak")
+    return v.value
 
 
 def profile_enable(on: bool = True):

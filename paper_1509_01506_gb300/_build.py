@@ -10,7 +10,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIBPATH = os.path.join(LIBDIR, "libdnadfa.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in (
     "scan_inst_pair.cu", "scan_inst_one_smem.cu", "scan_inst_one_global.cu", "scan_inst_hot.cu", "scan_inst_one_rep.cu",
-    "dna_scan.cu", "dna_batch.cu", "dna_map.cu", "dna_serve.cpp", "dna_compile.cpp", "dna_fasta.cpp")]
+    "dna_scan.cu", "dna_batch.cu", "dna_map.cu", "dna_bench.cu", "dna_serve.cpp", "dna_compile.cpp", "dna_fasta.cpp")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in (
     "dna_internal.h", "dna_runtime.h", "dna_device.cuh", "scan_kernel.cuh")] + \
     [os.path.join(ROOT, "include", "dna_dfa.h")]

@@ -203,3 +203,33 @@ def batched(n_seqs: int = 4096, n_dfas: int = 64, lo: int = 1024, hi: int = 16 *
         if state_range[0] <= n_states(r) <= state_range[1]:
             out.append(r)
     return buf, offs, out
+
+
+def serving(n_req: int = 4000, rate: float = 2000.0, n_states=None, payload_bytes: int = 256 * MiB):
+    """The serving workload: a 256 MiB order-2 Markov payload (seed 4) with 10% soft-masked
+    and 2% N runs; n_req requests with lengths log-uniform on [4 KiB, 64 MiB], offsets into
+    the payload, automaton indices and Poisson inter-arrival gaps (ns) at 'rate' per second
+    (seed 4); and 16 pattern sets: 8 sets of random 8..16-mers and 8 motif regexes. With
+    'n_states' (a callable giving a k-mer set's state count, supplied by the caller) each
+    k-mer set is shrunk by 4 until its automaton has at most 500 states.
+    Returns dict(payload, lens, offs, didx, gaps_ns, patterns=[("kmers", list) | ("regex", str)])."""
+    payload = markov2(4, payload_bytes)
+    overlay_runs(payload, 4, 0.10, 1000.0, "lower")
+    overlay_runs(payload, 5, 0.02, 50000.0, "N")
+    pats = []
+    for i in range(8):
+        n = 40
+        while True:
+            km = random_kmers(400 + i, n, 8, 16)
+            if n_states is None or n_states(km) <= 500 or n <= 4:
+                break
+            n -= 4
+        pats.append(("kmers", km))
+    for r in random_regexes(4, 8):
+        pats.append(("regex", r))
+    rng = np.random.Generator(np.random.PCG64(4))
+    lens = log_uniform_lengths(4, n_req, 4 * 1024, 64 * MiB)
+    offs = np.array([int(rng.integers(0, payload_bytes - n + 1)) for n in lens], np.int64)
+    didx = rng.integers(0, len(pats), n_req)
+    gaps = rng.exponential(1e9 / rate, n_req)
+    return dict(payload=payload, lens=lens, offs=offs, didx=didx, gaps_ns=gaps, patterns=pats)

@@ -480,3 +480,12 @@ def test_back_to_back_scans_on_two_streams_share_nothing_stale():
         assert int(c.item()) == want[k][0]
         if pos:
             assert np.array_equal(p[:want[k][0]].cpu().numpy(), want[k][1])
+
+
+def test_lookup_peak_microbenchmark():
+    """dna_lookup_peak measures the lookup rates the rooflines divide by: lanes in their
+    own banks beat lanes at random banks, and both beat random L2 gathers."""
+    p0, p1, p2 = dna.lookup_peak(0), dna.lookup_peak(1), dna.lookup_peak(2)
+    assert p0 > p1 > 0 and p0 > p2 > 0
+    with pytest.raises(dna.DnaError):
+        dna.lookup_peak(3)

@@ -165,3 +165,42 @@ def test_drain_with_a_short_limit_times_out_and_a_later_drain_completes(workload
         assert comps[rid]["status"] == 0
         assert comps[rid]["count"] == oracle.run(t, a, payload[off:off + n], positions=False)[0]
     assert comps[second]["admit_ns"] >= comps[second]["arrival_ns"]
+
+
+def test_bench_serving_sample_equals_the_oracle():
+    """A seeded sample of 64 requests of the bench's serving workload (the 16 resident
+    automata, the 256 MiB soft-masked payload with N runs, the largest requests near
+    64 MiB included), served through the request loop, gives the oracle's counts."""
+    w = synth.serving(n_states=lambda km: dna.compile_kmers(km)[0].shape[0])
+    lens, offs, didx = w["lens"], w["offs"], w["didx"]
+    rng = np.random.default_rng(77)
+    pick = set(np.argsort(lens)[-8:].tolist())                 # the largest requests
+    for k in range(16):                                         # one of every automaton
+        pick.add(int(np.flatnonzero(didx == k)[0]))
+    while len(pick) < 64:
+        pick.add(int(rng.integers(0, len(lens))))
+    pick = sorted(pick)
+    assert max(lens[i] for i in pick) > 60 * MiB
+    pinned = torch.from_numpy(w["payload"]).pin_memory()
+    dfas, tables = [], []
+    for kind, pat in w["patterns"]:
+        if kind == "kmers":
+            dfas.append(dna.Dfa.from_kmers(pat))
+            tables.append(oracle.compile_kmers(pat, minimise=True))
+        else:
+            dfas.append(dna.Dfa.from_regex(pat))
+            tables.append(oracle.compile_regex(pat))
+    srv = dna.Server(dfas, slots=8)
+    ids = {}
+    for i in pick:
+        ids[srv.submit((pinned.data_ptr() + int(offs[i]), int(lens[i])), int(didx[i]))] = i
+    srv.drain()
+    comps = srv.poll(256)
+    srv.free()
+    assert len(comps) == len(pick)
+    payload = w["payload"]
+    for c in comps:
+        i = ids[c["id"]]
+        assert c["status"] == 0
+        want = oracle.run(*tables[int(didx[i])], payload[int(offs[i]):int(offs[i]) + int(lens[i])], positions=False)[0]
+        assert c["count"] == want, (i, int(lens[i]), int(didx[i]))
