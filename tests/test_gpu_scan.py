@@ -489,3 +489,33 @@ def test_lookup_peak_microbenchmark():
     assert p0 > p1 > 0 and p0 > p2 > 0
     with pytest.raises(dna.DnaError):
         dna.lookup_peak(3)
+
+
+@pytest.mark.parametrize("plan", [None, dict(chunk_bytes=128), dict(chunk_bytes=256, lookback=12),
+                                  dict(chunk_bytes=384, warps_per_cta=8), dict(chunk_bytes=4096, lookback=1),
+                                  dict(warps_per_cta=16, lookback=30)], ids=str)
+def test_count_only_one_symbol_scans(plan):
+    """Count-only scans with the shared one-symbol table (the placement of the 3.2 GiB
+    workload's automaton): counts equal the oracle's across lengths, offsets, lookback
+    windows, resets, every byte value, automata that never meet, and the 7,366-state
+    Aho-Corasick automaton."""
+    plan = dict(plan or {}, placement=2)
+    rng = np.random.default_rng(61)
+    for n, off in ((1, 0), (130, 3), (4097, 1), (100003, 7), (2 * MiB + 77, 5)):
+        seq = noisy_markov(62 + n % 7, n) if n > 200 else synth.uniform(63, n)
+        check("regex", "|".join(synth.REGEX_DNA_TABLE_V), seq, offset=off, plan=plan, positions=False)
+    seq = rng.integers(0, 256, size=MiB + 3).astype(np.uint8)
+    bases = np.frombuffer(b"ACGTacgt", np.uint8)
+    pick = rng.random(seq.size) < 0.97
+    seq[pick] = bases[rng.integers(0, 8, size=int(pick.sum()))]
+    seq[200000:260000] = ord("N")
+    check("kmers", synth.random_kmers(64, 300, 6, 9), seq, offset=2, plan=plan, positions=False)
+    check("regex", "A(C|G)*T", noisy_markov(65, MiB + 9), plan=plan, positions=False)
+    table = rng.integers(0, 120, size=(120, 4)).astype(np.uint32)
+    acc = (rng.random(120) < 0.3).astype(np.uint8)
+    useq = synth.uniform(66, 300001)
+    want_c, _ = oracle.run(table.astype(np.int32), acc, useq, positions=False)
+    c, _ = gpu_run(dna.Dfa(table, dna.pack_accept(acc)), to_device(useq, 3), positions=False, plan=plan)
+    assert c == want_c
+    check("kmers", synth.random_kmers(6, 1000, 12), noisy_markov(67, 8 * MiB + 1, n_frac=0.02),
+          offset=1, plan=plan, positions=False)
