@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-plain-configs", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--profile-case", default=None,
+                    choices=["large_ac_512MiB", "map_perm8_256MiB", "map_perm64_64MiB", "batched_256x16"],
+                    help="run one case a few times for a profiler capture and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -623,9 +626,49 @@ def bench_plain_configs(dna, torch, stream, peak):
 
 
 
+def profile_case(name):
+    """One workload, a few launches, for an ncu capture (the profiles' commands)."""
+    import torch
+    import paper_1509_01506_gb300 as dna
+    import synth
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    if name == "large_ac_512MiB":
+        seq, kmers = synth.plain_large(n=512 * MiB)
+        dfa = dna.Dfa.from_kmers(kmers)
+        d = torch.from_numpy(seq).cuda()
+        runs = [lambda: dna.scan(dfa, d, out_count=cnt, plan=dict(placement=2))] * 5
+    elif name.startswith("map_perm"):
+        q, n = (8, 256 * MiB) if name == "map_perm8_256MiB" else (64, 64 * MiB)
+        rng = np.random.Generator(np.random.PCG64(q))
+        table = np.stack([rng.permutation(q) for _ in range(4)], axis=1).astype(np.uint32)
+        acc = (rng.random(q) < 0.25).astype(np.uint8)
+        acc[0] = 0
+        acc[int(rng.integers(1, q))] = 1
+        dfa = dna.Dfa(table, dna.pack_accept(acc))
+        d = torch.from_numpy(synth.plain_markov(n)[0]).cuda()
+        runs = [lambda: dna.scan(dfa, d, out_count=cnt)] * 5
+    else:   # batched_256x16: 256 sequences x 16 automata of the batched workload's recipe
+        buf, offs, regexes = synth.batched(n_seqs=256, n_dfas=16,
+                                           n_states=lambda r: dna.compile_regex(r)[0].shape[0])
+        dbuf = torch.from_numpy(buf).cuda()
+        lens = [int(offs[i + 1] - offs[i]) for i in range(offs.size - 1)]
+        starts = [dbuf.data_ptr() + int(offs[i]) for i in range(offs.size - 1)]
+        dfas = [dna.Dfa.from_regex(r) for r in regexes]
+        plan = dna.Batch(dfas, starts, lens=lens, autotune=False)
+        out = torch.empty((len(lens), len(dfas)), dtype=torch.int64, device="cuda")
+        runs = [lambda: plan.run(out)] * 5
+    for r in runs:
+        r()
+    torch.cuda.synchronize()
+    print(f"{name}: done", flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -65,23 +65,29 @@ struct MapParams {
     uint32_t k1, k5, lut_lo, lut_hi;
 };
 
-// One warp per (chunk, block of 32 start states). The chunk is cut into G equal parts
-// (32 / G lanes each) walked at once: lane (g, q) runs part g from state 32w + q (lanes at
-// or past n_states run from state 0 and are ignored), so that small automata keep every
-// lane busy. Each part's bytes are staged 512 at a time; lane k decodes word k of every
-// part's row for the warp. At the end the warp composes the parts' maps into the chunk's
-// map.
-template <int G, int TAB>
+// One warp per (chunk, block of 32 start states). Lanes form G groups of 32 / G; the
+// chunk is cut into G x C equal parts and lane (g, q) runs parts g, g + G, ..., (C of
+// them, side by side as independent chains) from state 32w + q (lanes at or past
+// n_states run from state 0 and are ignored), so that small automata keep every lane
+// busy and each lane has C lookups in flight. Each part's bytes are staged TILE at a
+// time; lane k decodes word k of every part's row for the warp. At the end the warp
+// composes the parts' maps, in order, into the chunk's map.
+template <int G, int TAB, int C>
 __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
-    static_assert(TAB == TAB_PAIR || G == 1, "parts only with the two-symbol table");
-    constexpr uint32_t kLanes = 32u / G;               // lanes (start states) per part
-    constexpr uint32_t kWarpStage = 2u * G * kMapTile; // double-buffered tile of every part
+    static_assert(TAB == TAB_PAIR || G * C == 1, "parts only with the two-symbol table");
+    constexpr uint32_t kParts = (uint32_t)(G * C);
+    constexpr uint32_t kLanes = 32u / G;               // lanes (start states) per group
+    // bytes of a part per stage: 512 for one chain, else 2 KiB shared by the parts
+    constexpr uint32_t TILE = C == 1 ? (uint32_t)kMapTile : 2048u / kParts;
+    constexpr uint32_t kRows = TILE / kTile;           // 128-byte rows per part per stage
+    constexpr uint32_t kWarpStage = 2u * kParts * TILE;   // double-buffered tile of every part
+    static_assert(kRows >= 1 && (kParts * TILE) % 512 == 0, "tile shape");
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t g = (uint32_t)lane / kLanes, q = (uint32_t)lane % kLanes;
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
-    // shared memory: [stages: warps x 2 x G x 512 B][one-symbol table: Q x 16 B][pad]
+    // shared memory: [stages: warps x 2 x parts x TILE][one-symbol table: Q x 16 B][pad]
     //                [replicated table: two-symbol 2 KiB or one-symbol 512 B per state]
     uint8_t *stage = smem + (size_t)warp * kWarpStage;
     const uint32_t stage_addr = smem_base + (uint32_t)warp * kWarpStage;
@@ -108,40 +114,72 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
     if (c >= p.n_chunks) return;   // warp-uniform; no barrier follows
     // decoded codes of the current row of every part (rows 36 words apart, so that parts
     // read by the same instruction sit in different banks)
-    __shared__ __align__(16) uint32_t ys_all[kMapWarps][G][36];
-    uint32_t *ys = ys_all[warp][g];
+    __shared__ __align__(16) uint32_t ys_all[kMapWarps][kParts][36];
 
     OneTable T;
     T.t = one_s;
     T.reset_entry = p.reset_entry;
     const uint64_t b = (uint64_t)c * p.chunk_bytes;
-    const uint64_t part = p.chunk_bytes / G;           // multiple of kMapTile
-    const uint64_t pb = b + g * part;                  // this lane's part
-    const uint64_t from = pb > p.lo ? pb : p.lo;
-    const uint64_t pe = pb + part < p.hi ? pb + part : p.hi;
-    const uint64_t to = pe > from ? pe : from;         // empty past the sequence end
+    const uint64_t part = p.chunk_bytes / kParts;      // multiple of TILE
     const uint64_t sub = p.chunk_bytes / kMapSubs;
-    const uint32_t ntiles = (uint32_t)(part / kMapTile);   // the same for every part and warp
+    const uint32_t ntiles = (uint32_t)(part / TILE);   // the same for every part and warp
     const uint32_t sq = wb * 32u + q;                  // this lane's start state
     const uint32_t q0 = sq < p.n_states ? sq : 0u;
-    auto cur_of = [&](uint32_t s) {
-        return TAB == TAB_PAIR ? tab_base + s * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u
-                               : tab_base + s * kOneRowBytes + (uint32_t)lane * 4u;
+    auto cur_of = [&](uint32_t st) {
+        return TAB == TAB_PAIR ? tab_base + st * (uint32_t)kPairRowBytes + (uint32_t)lane * 4u
+                               : tab_base + st * kOneRowBytes + (uint32_t)lane * 4u;
     };
     auto state_of = [&](uint32_t cv) {
         return TAB == TAB_PAIR ? ((cv & 0x3FFFFu) - tab_base) / (uint32_t)kPairRowBytes
                                : ((cv & 0x3FE00u) - tab_base) / kOneRowBytes;
     };
-    uint32_t cur = cur_of(q0);
-    uint32_t cnt = 0;
-    auto issue = [&](uint32_t t) {   // lane copies 16 bytes of tile t of every part (past hi: zero-filled)
+    // chain h of this lane: part g + G h, bytes [from[h], to[h])
+    uint64_t pb[C], from[C], to[C];
+    uint32_t cur[C], cnt[C];
 #pragma unroll
-        for (int gg = 0; gg < G; ++gg) {
-            const uint64_t off = b + (uint64_t)gg * part + (uint64_t)t * kMapTile + (uint64_t)lane * 16u;
+    for (int h = 0; h < C; ++h) {
+        pb[h] = b + (uint64_t)(g + (uint32_t)G * h) * part;
+        from[h] = pb[h] > p.lo ? pb[h] : p.lo;
+        const uint64_t pe = pb[h] + part < p.hi ? pb[h] + part : p.hi;
+        to[h] = pe > from[h] ? pe : from[h];           // empty past the sequence end
+        cur[h] = cur_of(q0);
+        cnt[h] = 0;
+    }
+    // lane copies 16-byte pieces of tile t of every part (past hi: zero-filled)
+    auto issue = [&](uint32_t t) {
+        constexpr uint32_t kPieces = kParts * TILE / 16u / 32u;   // per lane
+#pragma unroll
+        for (uint32_t j = 0; j < kPieces; ++j) {
+            const uint32_t idx = j * 32u + (uint32_t)lane;
+            const uint32_t pp = idx / (TILE / 16u), o = (idx % (TILE / 16u)) * 16u;
+            const uint64_t off = b + (uint64_t)pp * part + (uint64_t)t * TILE + o;
             const bool ok = off < p.hi;
-            cp_async16(stage_addr + ((t & 1u) * G + (uint32_t)gg) * kMapTile + (uint32_t)lane * 16u,
-                       ok ? p.abase + off : p.abase, ok ? 16u : 0u);
+            cp_async16(stage_addr + ((t & 1u) * kParts + pp) * TILE + o, ok ? p.abase + off : p.abase, ok ? 16u : 0u);
         }
+    };
+    // the pair walk of one 128-byte row (words from the decoded row 'ys') from 'cv'
+    auto pair_row = [&](const uint32_t *ys, uint32_t &cv, uint32_t &cn) {
+        uint32_t acc = 0, rc = 0, c2 = cv;
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4) {
+            const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
+            const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * k4 + i;
+                const uint32_t e1 = lds_u32(mux_pair(c2, yv[i]));
+                const uint32_t e2 = lds_u32(mux_pair(e1, yv[i] >> 16));
+                acc = mad_lo(e1, p.k1, acc);
+                acc = mad_lo(e2, p.k1, acc);
+                c2 = e2;
+                if (k % 3 == 2 || k == 31) {
+                    rc = mad_hi(acc, p.k5, rc);
+                    acc = 0;
+                }
+            }
+        }
+        cn += rc;
+        cv = c2 & 0x3FFFFu;
     };
     issue(0);
     cp_async_commit();
@@ -150,104 +188,141 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
         cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
-        const uint8_t *tiles = stage + (t & 1u) * G * kMapTile;
+        const uint8_t *tiles = stage + (t & 1u) * kParts * TILE;
 #pragma unroll 1
-        for (int r = 0; r < kMapTile / kTile; ++r) {
-            const uint64_t ro = pb + (uint64_t)t * kMapTile + (uint64_t)r * kTile;
-            if (p.bound && ro < to && (ro - b) % sub == 0)   // a sub-chunk starts here: record the state
-                p.bound[((uint64_t)c * kMapSubs + (ro - b) / sub) * p.qp + sq] = state_of(cur);
-            const uint8_t *row = tiles + g * kMapTile + r * kTile;
+        for (uint32_t r = 0; r < kRows; ++r) {
+            uint64_t ro[C];
+#pragma unroll
+            for (int h = 0; h < C; ++h) {
+                ro[h] = pb[h] + (uint64_t)t * TILE + (uint64_t)r * kTile;
+                if (p.bound && ro[h] < to[h] && (ro[h] - b) % sub == 0)   // a sub-chunk starts here
+                    p.bound[((uint64_t)c * kMapSubs + (ro[h] - b) / sub) * p.qp + sq] = state_of(cur[h]);
+            }
             // lane k decodes word k of each part's row for the warp: its codes (y, read
             // back by the part's lanes) and the base check (voted per part)
             uint32_t bad_parts = 0;
 #pragma unroll
-            for (int gg = 0; gg < G; ++gg) {
-                const uint32_t wk = *reinterpret_cast<const uint32_t *>(tiles + gg * kMapTile + r * kTile + 4 * lane);
+            for (uint32_t pp = 0; pp < kParts; ++pp) {
+                const uint32_t wk = *reinterpret_cast<const uint32_t *>(tiles + pp * TILE + r * kTile + 4 * lane);
                 const uint32_t xk = wk & 0x06060606u;
                 // two-symbol table: pairs at bits 7..10 and 23..26; one-symbol: raw codes
-                ys_all[warp][gg][lane] = TAB == TAB_PAIR ? mad_lo(xk, 65u, 0u) : xk;
+                ys_all[warp][pp][lane] = TAB == TAB_PAIR ? mad_lo(xk, 65u, 0u) : xk;
                 const uint32_t zk = xk | (xk >> 4);
                 const bool bad = ((__byte_perm(p.lut_lo, p.lut_hi, __byte_perm(zk, 0, 0x0020)) ^ wk) & 0xDFDFDFDFu) != 0;
-                bad_parts |= (__any_sync(0xFFFFFFFFu, bad) ? 1u : 0u) << gg;
+                bad_parts |= (__any_sync(0xFFFFFFFFu, bad) ? 1u : 0u) << pp;
             }
             __syncwarp();
-            const bool full = ro >= from && ro + kTile <= to;
-            if (full && !((bad_parts >> g) & 1u)) {
-                if (TAB == TAB_PAIR) {
-                    uint32_t acc = 0, rc = 0, c2 = cur;
+            bool fast[C];
 #pragma unroll
-                    for (int k4 = 0; k4 < 8; ++k4) {
-                        const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
-                        const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+            for (int h = 0; h < C; ++h)
+                fast[h] = ro[h] >= from[h] && ro[h] + kTile <= to[h] && !((bad_parts >> (g + G * h)) & 1u);
+            if (TAB == TAB_PAIR && C == 2 && fast[0] && fast[C - 1]) {
+                // both chains side by side: their lookups overlap
+                const uint32_t *ya = ys_all[warp][g], *yb = ys_all[warp][g + (C - 1) * G];
+                uint32_t acc0 = 0, acc1 = 0, rc0 = 0, rc1 = 0, a2 = cur[0], b2 = cur[C - 1];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int k = 4 * k4 + i;
-                            const uint32_t e1 = lds_u32(mux_pair(c2, yv[i]));
-                            const uint32_t e2 = lds_u32(mux_pair(e1, yv[i] >> 16));
-                            acc = mad_lo(e1, p.k1, acc);
-                            acc = mad_lo(e2, p.k1, acc);
-                            c2 = e2;
-                            if (k % 3 == 2 || k == 31) {
-                                rc = mad_hi(acc, p.k5, rc);
-                                acc = 0;
+                for (int k4 = 0; k4 < 8; ++k4) {
+                    const uint4 y4 = *reinterpret_cast<const uint4 *>(ya + 4 * k4);
+                    const uint4 z4 = *reinterpret_cast<const uint4 *>(yb + 4 * k4);
+                    const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w}, zv[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = 4 * k4 + i;
+                        const uint32_t e1 = lds_u32(mux_pair(a2, yv[i]));
+                        const uint32_t f1 = lds_u32(mux_pair(b2, zv[i]));
+                        const uint32_t e2 = lds_u32(mux_pair(e1, yv[i] >> 16));
+                        const uint32_t f2 = lds_u32(mux_pair(f1, zv[i] >> 16));
+                        acc0 = mad_lo(e1, p.k1, acc0);
+                        acc1 = mad_lo(f1, p.k1, acc1);
+                        acc0 = mad_lo(e2, p.k1, acc0);
+                        acc1 = mad_lo(f2, p.k1, acc1);
+                        a2 = e2;
+                        b2 = f2;
+                        if (k % 3 == 2 || k == 31) {
+                            rc0 = mad_hi(acc0, p.k5, rc0);
+                            rc1 = mad_hi(acc1, p.k5, rc1);
+                            acc0 = 0;
+                            acc1 = 0;
+                        }
+                    }
+                }
+                cnt[0] += rc0;
+                cnt[C - 1] += rc1;
+                cur[0] = a2 & 0x3FFFFu;
+                cur[C - 1] = b2 & 0x3FFFFu;
+            } else {
+#pragma unroll
+                for (int h = 0; h < C; ++h) {
+                    const uint32_t ph = g + (uint32_t)G * h;
+                    if (fast[h]) {
+                        if (TAB == TAB_PAIR) {
+                            pair_row(ys_all[warp][ph], cur[h], cnt[h]);
+                        } else {
+                            // byte j's code sits at bits 8j+1..8j+2 of y; the lookup puts it
+                            // at bits 7..8 of the row address
+                            const uint32_t *ys = ys_all[warp][ph];
+                            uint32_t rc = 0, e = cur[h];
+#pragma unroll
+                            for (int k4 = 0; k4 < 8; ++k4) {
+                                const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
+                                const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    const uint32_t y = yv[i];
+                                    e = lds_u32((e & kOneAddrMask) | ((y << 6) & 0x180u)); rc += e & 1u;
+                                    e = lds_u32((e & kOneAddrMask) | ((y >> 2) & 0x180u)); rc += e & 1u;
+                                    e = lds_u32((e & kOneAddrMask) | ((y >> 10) & 0x180u)); rc += e & 1u;
+                                    e = lds_u32((e & kOneAddrMask) | ((y >> 18) & 0x180u)); rc += e & 1u;
+                                }
                             }
+                            cnt[h] += rc;
+                            cur[h] = e & ~1u;
                         }
-                    }
-                    cnt += rc;
-                    cur = c2 & 0x3FFFFu;
-                } else {
-                    // byte j's code sits at bits 8j+1..8j+2 of y; the lookup puts it at bits
-                    // 7..8 of the row address
-                    uint32_t rc = 0, e = cur;
-#pragma unroll
-                    for (int k4 = 0; k4 < 8; ++k4) {
-                        const uint4 y4 = *reinterpret_cast<const uint4 *>(ys + 4 * k4);
-                        const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const uint32_t y = yv[i];
-                            e = lds_u32((e & kOneAddrMask) | ((y << 6) & 0x180u)); rc += e & 1u;
-                            e = lds_u32((e & kOneAddrMask) | ((y >> 2) & 0x180u)); rc += e & 1u;
-                            e = lds_u32((e & kOneAddrMask) | ((y >> 10) & 0x180u)); rc += e & 1u;
-                            e = lds_u32((e & kOneAddrMask) | ((y >> 18) & 0x180u)); rc += e & 1u;
+                    } else if (ro[h] + kTile > from[h] && ro[h] < to[h]) {
+                        // reset bytes or a sequence edge in this row: byte by byte
+                        const uint8_t *row = tiles + ph * TILE + r * kTile;
+                        uint32_t qs = state_of(cur[h]);
+                        const uint32_t k0 = ro[h] < from[h] ? (uint32_t)(from[h] - ro[h]) : 0u;
+                        const uint32_t k1 = ro[h] + kTile > to[h] ? (uint32_t)(to[h] - ro[h]) : (uint32_t)kTile;
+                        for (uint32_t k = k0; k < k1; ++k) {
+                            const uint32_t e = T.step(qs, row[k]);
+                            qs = e & 0x7FFFFFFFu;
+                            cnt[h] += e >> 31;
                         }
+                        cur[h] = cur_of(qs);
                     }
-                    cnt += rc;
-                    cur = e & ~1u;
                 }
-            } else if (ro + kTile > from && ro < to) {
-                // reset bytes or a sequence edge in this row: byte by byte
-                uint32_t qs = state_of(cur);
-                const uint32_t k0 = ro < from ? (uint32_t)(from - ro) : 0u;
-                const uint32_t k1 = ro + kTile > to ? (uint32_t)(to - ro) : (uint32_t)kTile;
-                for (uint32_t k = k0; k < k1; ++k) {
-                    const uint32_t e = T.step(qs, row[k]);
-                    qs = e & 0x7FFFFFFFu;
-                    cnt += e >> 31;
-                }
-                cur = cur_of(qs);
             }
             __syncwarp();   // ys is rewritten by the next row
         }
         __syncwarp();   // every lane is done with this stage before it is refilled
     }
     cp_async_wait<0>();
-    // compose the parts: from chunk start state s, part g starts where part g-1 ended
-    const uint32_t end = state_of(cur);
-    if (G == 1) {
-        p.map_end[(uint64_t)c * p.qp + sq] = end;
-        p.map_cnt[(uint64_t)c * p.qp + sq] = cnt;
+    // compose the parts in order: from chunk start state s, part pp starts where part
+    // pp - 1 ended; part pp is chain pp / G of group pp % G
+    uint32_t end[C];
+#pragma unroll
+    for (int h = 0; h < C; ++h) end[h] = state_of(cur[h]);
+    if (kParts == 1) {
+        p.map_end[(uint64_t)c * p.qp + sq] = end[0];
+        p.map_cnt[(uint64_t)c * p.qp + sq] = cnt[0];
         return;
     }
-    uint32_t s = q0, total = 0;
+    uint32_t st = q0, total = 0;
 #pragma unroll
-    for (int gg = 0; gg < G; ++gg) {
-        if (p.gstart && gg > 0 && g == 0) p.gstart[((uint64_t)c * G + gg) * 32u + q] = s;
-        total += __shfl_sync(0xFFFFFFFFu, cnt, gg * (int)kLanes + (int)s);
-        s = __shfl_sync(0xFFFFFFFFu, end, gg * (int)kLanes + (int)s);
+    for (uint32_t pp = 0; pp < kParts; ++pp) {
+        if (p.gstart && pp > 0 && g == 0) p.gstart[((uint64_t)c * kParts + pp) * 32u + q] = st;
+        const uint32_t hsel = pp / G;
+        uint32_t cv = cnt[0], ev = end[0];
+#pragma unroll
+        for (int h = 1; h < C; ++h)
+            if (hsel == (uint32_t)h) { cv = cnt[h]; ev = end[h]; }
+        const int src = (int)((pp % G) * kLanes + st);
+        total += __shfl_sync(0xFFFFFFFFu, cv, src);
+        st = __shfl_sync(0xFFFFFFFFu, ev, src);
     }
     if (g == 0) {
-        p.map_end[(uint64_t)c * 32u + q] = s;
+        p.map_end[(uint64_t)c * 32u + q] = st;
         p.map_cnt[(uint64_t)c * 32u + q] = total;
     }
 }
@@ -366,7 +441,10 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     // one wave of warps: every chunk takes wblocks of them
     const uint64_t tasks = (uint64_t)(pr.sms ? pr.sms : 152) * kMapWarps;
     const uint64_t unit = (uint64_t)kMapSubs * kTile;                        // 4 KiB
-    const uint32_t parts = d->n_states <= 8 ? 4u : d->n_states <= 16 ? 2u : 1u;
+    // lane groups of 8, 16 or 32 start states; two chains per lane up to 32 states
+    const uint32_t groups = d->n_states <= 8 ? 4u : d->n_states <= 16 ? 2u : 1u;
+    const uint32_t chains = d->n_states <= 32 ? 2u : 1u;
+    const uint32_t parts = groups * chains;
     const int tab = d->d_pair ? TAB_PAIR : TAB_ONE;
     const uint64_t want_chunks = std::max<uint64_t>(1, tasks / wblocks);
     uint64_t S = (total + want_chunks - 1) / want_chunks;
@@ -384,10 +462,22 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     const size_t o_gstart = positions ? take((size_t)n_chunks * 32 * parts * 4) : 0;
     const size_t o_given = positions ? take((size_t)n_chunks * kMapSubs * 4) : 0;
     const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
-    const size_t msmem = (size_t)kMapWarps * 2 * parts * kMapTile + (size_t)d->n_states * 16 + 2048 +
+    const size_t part_tile = chains == 1 ? (size_t)kMapTile : (size_t)2048 / parts;
+    const size_t msmem = (size_t)kMapWarps * 2 * parts * part_tile + (size_t)d->n_states * 16 + 2048 +
                          (size_t)d->n_states * (tab == TAB_PAIR ? (size_t)kPairRowBytes : (size_t)kOneRowBytes);
-    // static shared memory: the decoded rows, about 3.5 KB per part; 16 KB is reserved
-    if (msmem > optin - 16384) return DNA_ERR_CAPACITY;
+    void (*fn)(MapParams) = tab == TAB_ONE ? map_kernel<1, TAB_ONE, 1>
+                          : chains == 1 ? map_kernel<1, TAB_PAIR, 1>
+                          : groups == 4 ? map_kernel<4, TAB_PAIR, 2>
+                          : groups == 2 ? map_kernel<2, TAB_PAIR, 2> : map_kernel<1, TAB_PAIR, 2>;
+    // the kernel's static shared memory (its decoded rows, 3.5 KB per part) comes off the
+    // block's shared memory before the dynamic part
+    size_t static_smem = 0;
+    {
+        cudaFuncAttributes fa;
+        DNA_CUDA(cudaFuncGetAttributes(&fa, (const void *)fn));
+        static_smem = fa.sharedSizeBytes;
+    }
+    if (static_smem + 1024 >= optin || msmem > optin - static_smem - 1024) return DNA_ERR_CAPACITY;
     const uint32_t ng = (n_chunks + 31) / 32;
     const size_t jsmem = ((size_t)ng * (2 * qp + 1) + (qp == 32 ? (size_t)kJoinWarps * 2048 : 0)) * 4;
     if (jsmem > optin - 1024) return DNA_ERR_CAPACITY;
@@ -409,10 +499,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     mp.bound = positions ? (uint32_t *)(base + o_bound) : nullptr;
     mp.gstart = positions && parts > 1 ? (uint32_t *)(base + o_gstart) : nullptr;
     mp.k1 = 1u; mp.k5 = 32u; mp.lut_lo = 0x00630061u; mp.lut_hi = 0x00670074u;
-    void (*fn)(MapParams) = tab == TAB_ONE ? map_kernel<1, TAB_ONE>
-                          : parts == 4 ? map_kernel<4, TAB_PAIR>
-                          : parts == 2 ? map_kernel<2, TAB_PAIR> : map_kernel<1, TAB_PAIR>;
-    int rc = ensure_smem_optin((const void *)fn, d->device, optin - 16384);
+    int rc = ensure_smem_optin((const void *)fn, d->device, optin - static_smem - 1024);
     cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
     if (e == cudaSuccess) {
         const uint64_t n_tasks = (uint64_t)n_chunks * wblocks;
