@@ -55,6 +55,8 @@ def _load():
             lib.or_run.restype = i64
             lib.or_run_from.argtypes = [p, p, i32, i32, p, i64, p]
             lib.or_run_from.restype = i64
+            lib.or_run_piece.argtypes = [p, p, i32, i32, p, i64, p, p, i64]
+            lib.or_run_piece.restype = i64
             lib.or_compile_regex.argtypes = [cp, ctypes.c_int, p, p, i32]
             lib.or_compile_regex.restype = i32
             lib.or_compile_kmers.argtypes = [cp, ctypes.c_int, p, p, i32]
@@ -192,6 +194,23 @@ def run_from(table, accept, q_start: int, seq):
     c = _check(_load().or_run_from(table.ctypes.data, accept.ctypes.data, table.shape[0],
                                    q_start, s.ctypes.data, s.size, ctypes.byref(q_end)))
     return c, q_end.value
+
+
+def run_piece(table, accept, q_start: int, seq, cap: int | None = None):
+    """The run of one piece from 'q_start': (count, end state, positions int64 counted
+    from the piece's first byte)."""
+    table = np.ascontiguousarray(table, dtype=np.int32)
+    accept = np.ascontiguousarray(accept, dtype=np.uint8)
+    s = _as_bytes(seq)
+    q_end = ctypes.c_int32(0)
+    cap = 1024 if cap is None else cap
+    while True:
+        pos = np.empty(max(1, cap), dtype=np.int64)
+        c = _check(_load().or_run_piece(table.ctypes.data, accept.ctypes.data, table.shape[0], q_start,
+                                        s.ctypes.data, s.size, ctypes.byref(q_end), pos.ctypes.data, cap))
+        if c <= cap:
+            return c, q_end.value, pos[:c].copy()
+        cap = c
 
 
 def symbol_of_byte(b: int) -> int:

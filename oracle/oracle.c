@@ -103,6 +103,32 @@ int64_t or_run_from(const int32_t *table, const uint8_t *accept, int32_t n_state
     return count;
 }
 
+/*
+ * The run of one piece of a longer sequence (Sec. III-B: a chunk scanned from a given
+ * start state): as or_run_from, also writing the first pos_cap positions, counted from
+ * the piece's first byte.
+ */
+int64_t or_run_piece(const int32_t *table, const uint8_t *accept, int32_t n_states,
+                     int32_t q_start, const uint8_t *seq, int64_t n, int32_t *q_end,
+                     int64_t *pos_out, int64_t pos_cap)
+{
+    if (n_states <= 0 || !table || !accept || (n > 0 && !seq)) return OR_ERR_ARG;
+    if (q_start < 0 || q_start >= n_states) return OR_ERR_ARG;
+    int32_t q = q_start;
+    int64_t count = 0;
+    for (int64_t j = 0; j < n; j++) {
+        int s = or_symbol_of_byte(seq[j]);
+        q = (s == 4) ? 0 : table[(int64_t)q * 4 + s];
+        if (q < 0 || q >= n_states) return OR_ERR_ARG;
+        if (accept[q]) {
+            if (pos_out && count < pos_cap) pos_out[count] = j;
+            count++;
+        }
+    }
+    if (q_end) *q_end = q;
+    return count;
+}
+
 /* ------------------------------------------------------------ regex parser */
 
 enum { RX_SET = 1, RX_CAT, RX_ALT, RX_REP };

@@ -227,6 +227,27 @@ def test_chunked_join_reproduces_sequential_run():
         assert acc == total
 
 
+def test_piece_run_from_reached_state_matches_brute_force():
+    """A piece run from the state reached over a prefix w reports exactly the brute-force
+    matches of w + piece that end inside the piece, counted from the piece's start, and
+    ends where the run over w + piece ends (Sec. III-B: a chunk scanned from its true
+    start state)."""
+    rng = np.random.default_rng(21)
+    for trial in range(40):
+        k = int(rng.integers(3, 7))
+        pats = ["".join("ACGT"[x] for x in rng.integers(0, 4, size=k)) for _ in range(int(rng.integers(1, 6)))]
+        t, a = oracle.compile_kmers(pats)
+        w = random_seq(rng, int(rng.integers(0, 40)))
+        piece = random_seq(rng, int(rng.integers(0, 200)))
+        _, q, _ = oracle.run_piece(t, a, 0, w)
+        c, q_end, pos = oracle.run_piece(t, a, q, piece)
+        want = [j - len(w) for j in naive_kmer_positions(w + piece, pats) if j >= len(w)]
+        assert c == len(want) and list(pos) == want
+        assert q_end == oracle.run_from(t, a, 0, w + piece)[1]
+        if not w:
+            assert q == 0
+
+
 def test_reset_byte_splits_the_result():
     """A reset byte returns every run to q0, so the result on s1 N s2 is
     the result on s1 followed by the result on s2 shifted by len(s1) + 1."""
