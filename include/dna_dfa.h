@@ -194,6 +194,29 @@ int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dna_stream_t 
              uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity);
 
 /*
+ * dna_scan_from -- dna_scan of one piece of a longer sequence (Sec. III-B: a chunk of the
+ * input scanned from a given start state; the join of Sec. III-B.4 composes pieces).
+ *   start_state     the state the run is in before the piece's first byte (the caller's
+ *                   numbering, as in the table given to dfa_load; 0 for a whole sequence).
+ *                   The piece's first chunk starts there exactly; later chunks are
+ *                   speculated and repaired as in dna_scan.
+ *   out_last_state  device pointer or NULL; receives the state after the piece's last
+ *                   byte (the caller's numbering), which is start_state for len = 0.
+ *   out_count, out_positions, positions_capacity
+ *                   as dna_scan: accepting steps inside the piece, and their positions
+ *                   counted from the piece's first byte.
+ * Scanning the pieces of a sequence in order, each from the last state of the one before
+ * it, gives the whole sequence's count and, offset by each piece's start, its positions;
+ * scanning a piece from a guessed state and rescanning it when the guess was wrong gives
+ * the same (the multi-process join composes pieces that way).
+ * Asynchronous like dna_scan. Errors: DNA_ERR_INVALID_ARG (start_state >= n_states), and
+ * as dna_scan.
+ */
+int dna_scan_from(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, uint32_t start_state,
+                  dna_stream_t stream, uint64_t *out_count, uint32_t *out_last_state,
+                  uint64_t *out_positions, uint64_t positions_capacity);
+
+/*
  * dna_scan_labels -- dna_scan with per-pattern results, for an automaton loaded with
  * dfa_load_labeled (Alg. 1's count per accepting state, reported per pattern, Table V).
  *   out_count         as dna_scan: steps that land in a state with any label.

@@ -24,7 +24,7 @@ PLACE_AUTO, PLACE_SMEM_PAIR, PLACE_SMEM_ONE, PLACE_GLOBAL_ONE, PLACE_MAP, PLACE_
 
 EXPORTED = [
     "dfa_load", "dfa_free", "dfa_info", "dfa_analyze", "dna_scan", "dna_scan_planned", "dna_scan_batch",
-    "dna_scan_count_static", "dna_scan_host", "dfa_load_labeled", "dna_scan_labels",
+    "dna_scan_count_static", "dna_scan_host", "dna_scan_from", "dfa_load_labeled", "dna_scan_labels",
     "dna_compile_regex_set", "dfa_tune", "dna_lookup_peak",
     "dna_batch_create", "dna_batch_run", "dna_batch_info", "dna_batch_free",
     "dna_server_create", "dna_server_submit", "dna_server_poll", "dna_server_drain",
@@ -132,6 +132,8 @@ def lib():
         L.dna_scan_count_static.restype = i32
         L.dna_scan_host.argtypes = [p, p, u64, p, p, p, u64]
         L.dna_scan_host.restype = i32
+        L.dna_scan_from.argtypes = [p, p, u64, u32, p, p, p, p, u64]
+        L.dna_scan_from.restype = i32
         L.dfa_load_labeled.argtypes = [p, u32, p, u32, ctypes.POINTER(p)]
         L.dfa_load_labeled.restype = i32
         L.dna_scan_labels.argtypes = [p, p, u64, p, p, p, p, p, u64]
@@ -410,6 +412,35 @@ def scan(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None,
                         pos_ptr, cap)
     _check(rc, "dna_scan")
     return out_count, (out_positions if positions else None)
+
+
+def scan_from(dfa: Dfa, seq, start_state: int = 0, positions: bool = False,
+              capacity: int | None = None, stream=None, out=None):
+    """dna_scan_from on a CUDA uint8 tensor: the scan of one piece of a longer sequence,
+    starting in 'start_state'. Returns (count [1] int64, last state [1] int32, positions
+    counted from the piece's first byte, or None). 'out' (or None) supplies the three
+    output tensors (count, last, positions) to write into. Results are ready when the
+    stream completes."""
+    import torch
+    if not (isinstance(seq, torch.Tensor) and seq.is_cuda and seq.dtype == torch.uint8):
+        raise TypeError("seq must be a CUDA uint8 tensor")
+    if not seq.is_contiguous():
+        raise ValueError("seq must be contiguous")
+    dev = seq.device
+    if out is not None:
+        count, last, pos = out
+        cap = pos.numel() if (positions and pos is not None) else 0
+    else:
+        count = torch.empty(1, dtype=torch.int64, device=dev)
+        last = torch.empty(1, dtype=torch.int32, device=dev)
+        pos, cap = None, 0
+        if positions:
+            cap = int(capacity if capacity is not None else max(1024, seq.numel() // 256))
+            pos = torch.empty(cap, dtype=torch.int64, device=dev)
+    _check(lib().dna_scan_from(dfa.handle, seq.data_ptr(), seq.numel(), int(start_state),
+                               _stream_handle(stream), count.data_ptr(), last.data_ptr(),
+                               pos.data_ptr() if positions else None, cap), "dna_scan_from")
+    return count, last, (pos if positions else None)
 
 
 def scan_labels(dfa: Dfa, seq, positions: bool = False, capacity: int | None = None, stream=None):

@@ -335,12 +335,15 @@ struct JoinParams {
     uint32_t parts;             // G of the map kernel: parts per chunk
     uint32_t *given;            // [n_chunks * 32] exact start of each sub-chunk, or null
     uint64_t *out_count;
+    uint32_t start;             // the state the sequence starts in
+    uint32_t *out_last;         // null, or receives the state after the last byte
+    const uint32_t *perm_inv;   // null, or device -> caller state numbering (for out_last)
 };
 
 // Single block. Chunks are taken 32 at a time: the group's 32 maps are composed for all
 // start states (for maps 32 wide, a warp per group with its maps cached in shared memory
 // and lane q following start q; for wider maps, one thread per (group, start state)
-// reading the maps from global memory), thread 0 then chains the groups from state 0,
+// reading the maps from global memory), thread 0 then chains the groups from the start,
 // and (for the positions pass) each group is walked again from its true start to give
 // every chunk's, and so every sub-chunk's, exact start.
 __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams p) {
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t s = 0;
+        uint32_t s = p.start;
         unsigned long long total = 0;
         for (uint32_t g = 0; g < ng; ++g) {
             g_start[g] = s;
@@ -401,6 +404,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
             s = g_end[g * qp + s];
         }
         *p.out_count = total;
+        if (p.out_last) *p.out_last = p.perm_inv ? p.perm_inv[s] : s;
     }
     __syncthreads();
     if (!p.given) return;
@@ -430,7 +434,8 @@ namespace dnalib {
 // ceil(Q / 32) warps per chunk. 'ext' (count only) supplies the scratch instead of the
 // library's pool: ext_bytes of device memory; DNA_ERR_CAPACITY when it is too small.
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream, uint64_t *out_count,
-                  uint64_t *out_positions, uint64_t cap, uint8_t *ext, size_t ext_bytes, const LabelOut *lab) {
+                  uint64_t *out_positions, uint64_t cap, uint8_t *ext, size_t ext_bytes, const LabelOut *lab,
+                  const ScanFrom *from) {
     if (d->n_states > kMaxMapStates) return DNA_ERR_INVALID_ARG;
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;
@@ -514,6 +519,9 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     jp.n_chunks = n_chunks; jp.n_states = d->n_states; jp.qp = qp; jp.parts = parts;
     jp.given = positions ? (uint32_t *)(base + o_given) : nullptr;
     jp.out_count = out_count;
+    jp.start = from ? from->start : 0u;
+    jp.out_last = from ? from->out_last : nullptr;
+    jp.perm_inv = d->d_perm_inv;
     if (e == cudaSuccess) {
         rc = ensure_smem_optin((const void *)map_join_kernel, d->device, optin - 1024);
         if (rc) e = cudaErrorInvalidValue;
@@ -530,7 +538,8 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
         dna_plan pl = {};
         pl.chunk_bytes = (uint32_t)(S / kMapSubs);
         pl.placement = d->d_pair ? DNA_PLACE_SMEM_PAIR : 0u;
-        rc = scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, &pl, jp.given, lab);
+        rc = scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, &pl, jp.given, lab,
+                             from);
     }
     if (!ext) {
         const int rf = scratch_free(mem, stream);

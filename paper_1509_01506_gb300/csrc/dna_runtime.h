@@ -32,6 +32,7 @@ struct dna_dfa {
     uint16_t *d_hot2 = nullptr;
     uint16_t *d_hot1 = nullptr;
     std::vector<uint32_t> perm;
+    uint32_t *d_perm_inv = nullptr;   // [n_states] device -> caller numbering (when renumbered)
     double hot_cover = 0;         // visit share of the hot rows that fit (random walk)
     // resident blocks per SM of each scan kernel variant with this automaton's shared
     // memory footprint ([mode][warp option][positions]; 0 = not yet queried)
@@ -80,22 +81,32 @@ struct LabelOut {
     uint32_t n_labels = 0;
 };
 
+// A scan of a piece of a longer sequence (dna_scan_from): the state the piece starts in
+// (device numbering) and where to write the state after it (caller's numbering), or null.
+struct ScanFrom {
+    uint32_t start = 0;
+    uint32_t *out_last = nullptr;
+};
+
 // The single-sequence scan behind dna_scan / dna_scan_planned (dispatches to the
-// chunk-map path for automata that need it). 'lab' (or null) asks for per-label outputs.
+// chunk-map path for automata that need it). 'lab' (or null) asks for per-label outputs;
+// 'from' (or null: start in q0, no last state) for a piece of a longer sequence.
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
-              const LabelOut *lab = nullptr);
+              const LabelOut *lab = nullptr, const ScanFrom *from = nullptr);
 // The speculative chunk scan; 'given_start' (per chunk, or null) supplies exact chunk
 // start states, in which case nothing is speculated or repaired.
 int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                     uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
-                    const uint32_t *given_start, const LabelOut *lab = nullptr);
+                    const uint32_t *given_start, const LabelOut *lab = nullptr,
+                    const ScanFrom *from = nullptr);
 // The chunk-map scan (dna_map.cu); n_states <= kMaxMapStates. 'ext' (count only, or
 // null) is caller-provided scratch of ext_bytes bytes used instead of the library's pool.
 constexpr uint32_t kMaxMapStates = 256;
 int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                   uint64_t *out_count, uint64_t *out_positions, uint64_t cap,
-                  uint8_t *ext = nullptr, size_t ext_bytes = 0, const LabelOut *lab = nullptr);
+                  uint8_t *ext = nullptr, size_t ext_bytes = 0, const LabelOut *lab = nullptr,
+                  const ScanFrom *from = nullptr);
 
 // Kernel timing: prof_begin records an event on the stream when profiling is enabled
 // (otherwise returns an empty token); prof_end records the closing event.

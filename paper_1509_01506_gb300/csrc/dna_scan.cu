@@ -64,6 +64,7 @@ struct EmitParams {
     uint64_t *out;
     uint64_t cap;
     uint32_t lut_lo, lut_hi;   // expected lowercase bytes per code, for the base check
+    uint32_t start_state;   // the state the first chunk starts in
     // per-label outputs (null labels: none): every hit row is walked, whatever the
     // capacity, and each accepting step's label mask is added into label_counts
     const uint32_t *labels;
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             const uint64_t b = cj * S;
             const uint64_t from = b > p.lo ? b : p.lo;
             const uint64_t to = b + S < p.hi ? b + S : p.hi;
-            uint32_t q = cj ? p.last_state[cj - 1] : 0u;
+            uint32_t q = cj ? p.last_state[cj - 1] : p.start_state;
             for (uint64_t rs = b; rs < to && (o < p.cap || lab); rs += kTile) {
                 uint32_t k0, k1;
                 row_span(rs, from, to, k0, k1);
@@ -438,6 +439,12 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
 }
 
 __global__ void write_zero_kernel(uint64_t *out) { *out = 0; }
+
+// An empty sequence (or piece): no match, and the run ends where it started.
+__global__ void write_empty_kernel(uint64_t *out, uint32_t *out_last, uint32_t last) {
+    *out = 0;
+    if (out_last) *out_last = last;
+}
 
 }  // namespace
 
@@ -837,9 +844,23 @@ void carve(Scratch &s, uint64_t nseg, uint64_t nblocks, bool positions, uint32_t
 
 namespace dnalib {
 
+// The outputs of an empty scan (the start state in the caller's numbering as the last).
+int write_empty(cudaStream_t stream, uint64_t *out_count, const dna_dfa *d, const ScanFrom *from) {
+    uint32_t last = 0;
+    if (from) {
+        last = from->start;
+        if (!d->perm.empty())
+            for (uint32_t q = 0; q < d->n_states; ++q)
+                if (d->perm[q] == from->start) { last = q; break; }
+    }
+    write_empty_kernel<<<1, 1, 0, stream>>>(out_count, from ? from->out_last : nullptr, last);
+    record_launch();
+    return cuda_status(cudaGetLastError());
+}
+
 int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
               uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
-              const LabelOut *lab) {
+              const LabelOut *lab, const ScanFrom *from) {
     if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
     const uint32_t req = ov ? ov->placement : 0u;
     if (req > DNA_PLACE_SMEM_ONE_REP) return DNA_ERR_INVALID_ARG;
@@ -849,29 +870,21 @@ int scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t s
         int cur_dev = -1;
         DNA_CUDA(cudaGetDevice(&cur_dev));
         if (cur_dev != d->device) return DNA_ERR_INVALID_ARG;
-        if (len == 0) {
-            write_zero_kernel<<<1, 1, 0, stream>>>(out_count);
-            record_launch();
-            return cuda_status(cudaGetLastError());
-        }
-        return map_scan_impl(d, seq, len, stream, out_count, out_positions, cap, nullptr, 0, lab);
+        if (len == 0) return write_empty(stream, out_count, d, from);
+        return map_scan_impl(d, seq, len, stream, out_count, out_positions, cap, nullptr, 0, lab, from);
     }
-    return scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, ov, nullptr, lab);
+    return scan_impl_given(d, seq, len, stream, out_count, out_positions, cap, ov, nullptr, lab, from);
 }
 
 int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream_t stream,
                     uint64_t *out_count, uint64_t *out_positions, uint64_t cap, const dna_plan *ov,
-                    const uint32_t *given_start, const LabelOut *lab) {
+                    const uint32_t *given_start, const LabelOut *lab, const ScanFrom *from) {
     if (!d || !out_count || (len > 0 && !seq)) return DNA_ERR_INVALID_ARG;
     if (len > (1ull << 40)) return DNA_ERR_INVALID_ARG;
     int cur_dev = -1;
     DNA_CUDA(cudaGetDevice(&cur_dev));
     if (cur_dev != d->device) return DNA_ERR_INVALID_ARG;
-    if (len == 0) {
-        write_zero_kernel<<<1, 1, 0, stream>>>(out_count);
-        record_launch();
-        return cuda_status(cudaGetLastError());
-    }
+    if (len == 0) return write_empty(stream, out_count, d, from);
     const uint64_t shift = (uint64_t)((uintptr_t)seq & 15u);
     const uint8_t *abase = seq - shift;
     const uint64_t total = len + shift;
@@ -906,6 +919,9 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
     sp.prefetch_tiles = pl.prefetch;
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.reset_ctrl = sctrl ? 1u : 0u;
+    sp.start_state = from ? from->start : 0u;
+    sp.out_last = from ? from->out_last : nullptr;
+    sp.perm_inv = d->d_perm_inv;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
     sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
     sp.k1 = 1u; sp.k5 = 1u << 5;
@@ -944,6 +960,7 @@ int scan_impl_given(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStre
         ep.spec_start = s.spec_start; ep.fix_delta = s.fix_delta;
         ep.flags = s.flags; ep.cta_off = s.cta_off; ep.out = out_positions; ep.cap = cap;
         ep.lut_lo = 0x00630061u; ep.lut_hi = 0x00670074u;
+        ep.start_state = sp.start_state;
         ep.labels = lab ? lab->labels : nullptr;
         ep.label_counts = lab ? lab->counts : nullptr;
         ep.pos_labels = lab ? lab->pos_labels : nullptr;
@@ -1139,11 +1156,20 @@ extern "C" int dfa_load(const uint32_t *table, uint32_t n_states, const uint8_t 
         if (e == cudaSuccess) e = device_alloc((void **)&d->d_hot1, sizeof(uint16_t) * h1.size());
         if (e == cudaSuccess) e = cudaMemcpy(d->d_hot1, h1.data(), sizeof(uint16_t) * h1.size(), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && !d->perm.empty()) {
+        // device -> caller numbering, for the last state a piece's scan reports
+        std::vector<uint32_t> inv(n_states);
+        for (uint32_t q = 0; q < n_states; ++q) inv[d->perm[q]] = q;
+        e = device_alloc((void **)&d->d_perm_inv, sizeof(uint32_t) * n_states);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d->d_perm_inv, inv.data(), sizeof(uint32_t) * n_states, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(d->d_one);
         cudaFree(d->d_pair);
         cudaFree(d->d_hot2);
         cudaFree(d->d_hot1);
+        cudaFree(d->d_perm_inv);
         delete d;
         return cuda_status(e);
     }
@@ -1187,6 +1213,7 @@ extern "C" void dfa_free(dna_dfa *d) {
     cudaFree(d->d_hot2);
     cudaFree(d->d_hot1);
     cudaFree(d->d_labels);
+    cudaFree(d->d_perm_inv);
     delete d;
 }
 
@@ -1229,6 +1256,17 @@ extern "C" int dna_scan(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, dn
                         uint64_t *out_count, uint64_t *out_positions, uint64_t positions_capacity) {
     return scan_impl(dfa, seq, len, (cudaStream_t)stream, out_count, out_positions,
                      positions_capacity, nullptr);
+}
+
+extern "C" int dna_scan_from(const dna_dfa *dfa, const uint8_t *seq, uint64_t len, uint32_t start_state,
+                             dna_stream_t stream, uint64_t *out_count, uint32_t *out_last_state,
+                             uint64_t *out_positions, uint64_t positions_capacity) {
+    if (!dfa || start_state >= dfa->n_states) return DNA_ERR_INVALID_ARG;
+    ScanFrom from;
+    from.start = dfa->perm.empty() ? start_state : dfa->perm[start_state];
+    from.out_last = out_last_state;
+    return scan_impl(dfa, seq, len, (cudaStream_t)stream, out_count, out_positions, positions_capacity,
+                     nullptr, nullptr, &from);
 }
 
 extern "C" int dna_scan_host(const dna_dfa *dfa, const uint8_t *seq_host, uint64_t len,
@@ -1412,6 +1450,9 @@ extern "C" int dna_scan_count_static(const dna_dfa *d, const uint8_t *seq, uint6
     sp.prefetch_tiles = pl.prefetch;
     sp.ctrl = s.ctrl; sp.pending = s.pending; sp.pending_cap = pending_cap;
     sp.reset_ctrl = 0u;
+    sp.start_state = 0u;
+    sp.out_last = nullptr;
+    sp.perm_inv = nullptr;
     sp.div_list = s.div_list; sp.div_cap = div_cap;
     sp.cta_sum = s.cta_sum; sp.cta_off = s.cta_off; sp.block_head = s.block_head; sp.out_count = out_count;
     sp.k1 = 1u; sp.k5 = 1u << 5;

@@ -80,6 +80,9 @@ struct ScanParams {
     // every state (read as 32-bit words)
     const uint32_t *hot2, *hot1;
     uint32_t hot_rows;
+    uint32_t start_state;   // the state the first chunk starts in (q0 for a whole sequence)
+    uint32_t *out_last;     // null, or receives the state after the last byte
+    const uint32_t *perm_inv;   // null, or device -> caller state numbering (for out_last)
 };
 
 using ScanFn = void (*)(ScanParams);
@@ -334,6 +337,10 @@ __device__ void finalize_block(const ScanParams &p, const OneTable &T, unsigned 
     }
     if (tid == 0) {
         *p.out_count = carry;
+        if (p.out_last) {
+            const uint32_t l = p.last_state[p.nseg - 1];
+            *p.out_last = p.perm_inv ? p.perm_inv[l] : l;
+        }
         // every other block took its ticket before this one, after its last use of the
         // control words: leave them zero for the next scan on this stream
         if (p.reset_ctrl)
@@ -510,6 +517,8 @@ scan_kernel(ScanParams p) {
     if (p.given_start) {
         // the chunk's exact start is known (computed from per-chunk state maps)
         if (active) q = p.given_start[seg];
+    } else if (seg == 0) {
+        q = p.start_state;   // the first chunk's start is known
     } else if (has_lookback) {   // the 'lookback' bytes in front of the chunk
         const uint64_t from = b - p.lo > p.lookback ? b - p.lookback : p.lo;
         for (uint64_t off = from; off < b; ++off) q = T.step(q, p.abase[off]) & 0x7FFFFFFFu;

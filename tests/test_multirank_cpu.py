@@ -75,3 +75,92 @@ def test_two_gloo_ranks_assemble_the_single_process_result(tmp_path):
     slowest, total = open(out + ".txt").read().split()
     assert float(slowest) == 2.0
     assert int(float(total)) == sum(s.size for s in seqs)
+
+
+# ------------------------------------------- one sequence split across ranks (the join)
+
+
+def test_join_step_chains_each_start_to_the_left_neighbours_last_state():
+    starts, agreed = shard.join_step([(0, 3, 5), (3, 1, 2), (4, 2, 7)])
+    assert starts == [0, 3, 1] and not agreed
+    starts, agreed = shard.join_step([(0, 3, 5), (3, 1, 2), (1, 2, 7)])
+    assert starts == [0, 3, 1] and agreed
+    assert shard.join_step([(0, 9, 1)]) == ([0], True)
+
+
+def _counter_table(m=5):
+    """A non-converging automaton: the number of A's mod m (every symbol permutes the
+    states, so no window fixes the start state and speculation from q0 is usually wrong)."""
+    t = np.array([[(q + 1) % m, q, q, q] for q in range(m)], dtype=np.int32)
+    a = np.zeros(m, dtype=np.uint8)
+    a[0] = 1
+    return t, a
+
+
+def _split_case(kind):
+    import oracle
+    import synth
+    seq = synth.markov2(77, 60_000)
+    if kind == "kmer":
+        t, a = oracle.compile_kmers(["ACGTA", "TTGCA", "GATTACA"])
+    else:
+        t, a = _counter_table()
+    return seq, t, a
+
+
+def _join_worker(rank, world, port, out_path, kind, use_prefix):
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        seq, t, a = _split_case(kind)
+        cuts = [seq.size * r // world for r in range(world + 1)]
+        lo, hi = cuts[rank], cuts[rank + 1]
+        piece = seq[lo:hi]
+
+        def scan_piece(q):
+            c, last, pos = oracle.run_piece(t, a, q, piece)
+            return c, last, pos
+
+        guess = 0
+        if use_prefix and rank > 0:
+            guess = oracle.run_piece(t, a, 0, seq[max(0, lo - 64):lo])[1]
+        r = shard.scan_sharded(scan_piece, offset=lo, guess=guess)
+        np.save(f"{out_path}.{rank}.npy", r["positions"])
+        with open(f"{out_path}.{rank}.txt", "w") as f:
+            f.write(f"{r['count']} {r['local_count']} {r['start']} {r['last']} {r['rounds']} {r['rescans']}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,kind,use_prefix", [(2, "kmer", True), (3, "kmer", False), (3, "counter", False),
+                                                   (2, "counter", True)])
+def test_gloo_ranks_join_one_sequence_split_across_them(tmp_path, world, kind, use_prefix):
+    """Each rank scans its piece from a speculated start; the exchanged summaries repair
+    every wrong start, and the joined result equals the whole sequence's run."""
+    import oracle
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "join")
+    mp.start_processes(_join_worker, args=(world, _free_port(), out, kind, use_prefix), nprocs=world,
+                       join=True, start_method="spawn")
+    seq, t, a = _split_case(kind)
+    want_c, want_pos = oracle.run(t, a, seq)
+    pos = np.concatenate([np.load(f"{out}.{r}.npy") for r in range(world)])
+    rows = [open(f"{out}.{r}.txt").read().split() for r in range(world)]
+    assert all(int(x[0]) == want_c for x in rows)
+    assert sum(int(x[1]) for x in rows) == want_c
+    assert np.array_equal(pos, want_pos)
+    cuts = [seq.size * r // world for r in range(world + 1)]
+    for r in range(world):
+        true_start = oracle.run_from(t, a, 0, seq[:cuts[r]])[1]
+        assert int(rows[r][2]) == true_start
+        assert int(rows[r][3]) == oracle.run_from(t, a, 0, seq[:cuts[r + 1]])[1]
+    rounds = {int(x[4]) for x in rows}
+    assert len(rounds) == 1 and rounds.pop() <= world
+    if kind == "kmer" and use_prefix:
+        # a 64-byte prefix exceeds the definite depth: the speculation is exact
+        assert all(int(x[4]) == 1 and int(x[5]) == 0 for x in rows)
+    if kind == "counter":
+        assert any(int(x[5]) > 0 for x in rows)   # some start was wrong and repaired
