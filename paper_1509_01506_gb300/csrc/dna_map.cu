@@ -5,10 +5,12 @@
 // on DNA (permutation-like tables, counters): there every chunk's repair walks the whole
 // chunk and every join cascades, serially. For those the scan follows the paper's
 // possible-starting-state approach in full (Sec. III-A): a chunk is run from every state
-// at once. A warp runs one chunk from 32 start states (lane q from state 32w + q for the
-// warp's state block w); automata of more than 32 states give each chunk ceil(Q / 32)
-// warps, and automata of at most 8 or 16 states cut the chunk into 4 or 2 parts walked
-// side by side by lane groups, whose maps the warp composes. Each chunk yields a map (end
+// at once. Automata of at most 8 states keep all 8 runs of a lane in one register
+// (map_nib_kernel below: a lane walks one of the chunk's 32 parts). Larger ones: a warp
+// runs one chunk from 32 start states (lane q from state 32w + q for the warp's state
+// block w); automata of more than 32 states give each chunk ceil(Q / 32) warps, and
+// automata of at most 16 states cut the chunk into 2 parts walked side by side by lane
+// groups, whose maps the warp composes. Each chunk yields a map (end
 // state and count per start state) and, for the positions pass, the state at each of its
 // 32 sub-chunk boundaries per start state. A single-block join composes the maps in order
 // (chunk c starts in the end state of chunk c-1 from its true start), which gives the
@@ -62,6 +64,8 @@ struct MapParams {
                                 //   (null for a count-only scan)
     uint32_t *gstart;           // [n_chunks][G][32]: state at the start of part g per chunk start
                                 //   state (G > 1; null for a count-only scan)
+    uint32_t *cpre;             // map_nib_kernel, positions pass: [n_chunks][8] state at each
+                                //   chunk's start per start state of its block (else null)
     uint32_t k1, k5, lut_lo, lut_hi;
 };
 
@@ -327,6 +331,284 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
     }
 }
 
+// ---- Automata of at most 8 states: the runs from all 8 start states as one word.
+//
+// A lane walks one part of the chunk (a warp's 32 lanes walk its 32 parts, which are also
+// the positions pass's sub-chunks) and follows every start state at once: the state of
+// the run from each start sits in a 4-bit field of one register. A two-symbol step looks
+// up the pair's 8-byte row (byte j: the state two symbols after state j, and the
+// accepting steps on the way, << 4) and moves every run through it with two byte
+// permutes: permute(row, fields 0..3) gives the new states of fields 0..3 as bytes, and
+// permute(row, fields 4..7) those of fields 4..7, which are packed back as
+// (fields 0..3 bytes) | (fields 4..7 bytes << 4). The packing moves the run in field i
+// to field rotl3(i) (i = 0..3 go to 0, 2, 4, 6 and i = 4..7 to 1, 3, 5, 7), a
+// permutation of period 3, so a row starts with field s holding the run from s and the
+// step number mod 3 tells where each run is; the count bytes of each step are kept per
+// step number mod 3 and sorted back to runs at the end of the row. The 16 rows of the
+// pair table fill one 128-byte line, so the lanes' lookups never conflict in shared
+// memory. The warp then composes its 32 part maps with a prefix scan: the last lane's
+// result is the chunk map, and every lane's exclusive prefix is the state at its part's
+// start for each chunk start state (the positions pass's sub-chunk starts).
+constexpr int kNibWarps = 24;
+constexpr uint32_t kStageBytesNib = 32u * kTile;   // one 128-byte row of each of 32 parts
+
+// byte permute with a selector whose fields never have bit 3 set (plain byte copies)
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+__device__ __forceinline__ uint2 lds_v2(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
+// Inclusive prefix composition across the lanes of a warp (Kogge-Stone): lane i holds
+// the map of item i (e: end state per start state, cn: accepting steps per start state)
+// and ends with the composition of items 0..i. 'own' is this lane's 16-word scratch row
+// in shared memory (the lookups by state).
+__device__ __forceinline__ void compose_prefix(uint32_t (&e)[8], uint32_t (&cn)[8], uint32_t *own, int lane) {
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t pe_[8], pc_[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            pe_[s] = __shfl_up_sync(0xFFFFFFFFu, e[s], d);
+            pc_[s] = __shfl_up_sync(0xFFFFFFFFu, cn[s], d);
+            own[s] = e[s];
+            own[8 + s] = cn[s];
+        }
+        __syncwarp();
+        if (lane >= d) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t m = pe_[s];
+                e[s] = own[m];
+                cn[s] = pc_[s] + own[8 + m];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ __align__(128) uint2 tab2[16];   // pair rows, pair index = code1 + 4 x code2
+    __shared__ __align__(8) uint2 tab1[5];      // one-symbol rows, index code (4: a reset byte)
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t Q = p.n_states;
+    // byte j of a row: next state | accepting steps << 4; fields past n_states stay put
+    if (threadIdx.x < 21) {
+        const uint32_t i = threadIdx.x;
+        uint32_t lo = 0, hi = 0;
+        for (uint32_t j = 0; j < 8; ++j) {
+            uint32_t v = j;
+            if (j < Q) {
+                if (i < 16) {
+                    const uint32_t e1 = p.one[j * 4u + (i & 3u)];
+                    const uint32_t q1 = e1 & 0x7FFFFFFFu;
+                    const uint32_t e2 = p.one[q1 * 4u + (i >> 2)];
+                    v = (e2 & 0x7FFFFFFFu) | (((e1 >> 31) + (e2 >> 31)) << 4);
+                } else if (i < 20) {
+                    const uint32_t e1 = p.one[j * 4u + (i - 16u)];
+                    v = (e1 & 0x7FFFFFFFu) | ((e1 >> 31) << 4);
+                } else {
+                    v = (p.reset_entry >> 31) << 4;   // a reset: q0 (and whether it accepts)
+                }
+            }
+            if (j < 4) lo |= v << (8 * j);
+            else hi |= v << (8 * (j - 4));
+        }
+        if (i < 16) tab2[i] = make_uint2(lo, hi);
+        else tab1[i - 16] = make_uint2(lo, hi);
+    }
+    __syncthreads();
+    // warps past the last chunk walk nothing (identity maps) and join the block's
+    // composition below
+    const uint32_t c = blockIdx.x * kNibWarps + warp;
+    const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
+    uint8_t *stage_ptr = smem + (size_t)warp * kStageBytesNib;
+    const uint32_t stage_addr = smem_base + (uint32_t)warp * kStageBytesNib;
+    const uint32_t tab2_addr = (uint32_t)__cvta_generic_to_shared(tab2);
+    const uint64_t b = (uint64_t)c * p.chunk_bytes;
+    const uint64_t part = p.chunk_bytes / 32u;          // multiple of kTile
+    const uint64_t pb = b + (uint64_t)lane * part;
+    const uint64_t from = pb > p.lo ? pb : p.lo;
+    const uint64_t pe = pb + part < p.hi ? pb + part : p.hi;
+    const uint64_t to = pe > from ? pe : from;           // empty past the sequence end
+    const uint32_t ntiles = (uint32_t)(part / kTile);
+    // run-time constants: the multiplies and high multiplies that use them (shifts) stay
+    // on the multiply-add pipe, beside the byte permutes and logic on the integer pipe
+    const uint32_t k1 = p.k1, k16 = p.k5 >> 1, k65 = p.k1 * 65u;
+    const uint32_t h16 = p.k5 << 11, h28 = p.k5 << 23, h12 = p.k5 << 7;   // x >> 16, >> 4, >> 20
+    // staging: tile t of the 32 parts into a swizzled [32 rows][128 B] stage (16-byte
+    // column c of row r at slot c ^ (r & 7)); copy j of a lane moves column lane & 7 of
+    // row 4j + lane / 8, so each copy instruction covers four whole 128-byte lines
+    const uint32_t l8 = (uint32_t)lane >> 3, cc = (uint32_t)lane & 7u;
+    auto issue = [&](uint32_t t) {
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t r = 4u * j + l8;
+            const uint64_t off = b + (uint64_t)r * part + (uint64_t)t * kTile + cc * 16u;
+            const bool ok = off < p.hi;
+            cp_async16(stage_addr + r * kTile + ((cc ^ (r & 7u)) << 4), ok ? p.abase + off : p.abase, ok ? 16u : 0u);
+        }
+    };
+    // one step of every run: fields 0..3 and 4..7 through the row (lo, hi); returns the
+    // count bytes of fields 0..3 (ca) and 4..7 (cb)
+    auto step = [&](uint32_t &R, uint2 row, uint32_t &ca, uint32_t &cb) {
+        const uint32_t A = prmt(row.x, row.y, R);
+        const uint32_t B = prmt(row.x, row.y, __umulhi(R, h16));
+        const uint32_t B16 = mad_lo(B, k16, 0u);
+        uint32_t r;   // (A & 0x07070707) | (B16 & ~0x07070707), one lop3
+        asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(r) : "r"(A), "r"(B16), "r"(0x07070707u));
+        R = r;
+        ca = __umulhi(A, h28) & 0x03030303u;
+        cb = __umulhi(B, h28) & 0x03030303u;
+    };
+    const uint2 ident = make_uint2(0x03020100u, 0x07060504u);
+    uint32_t R = 0x76543210u;   // field s: the run from start state s
+    uint32_t tot[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) tot[s] = 0;
+    // count bytes of one phase (step number mod 3) -> per-run byte sums: run s sits in
+    // field rotl3^ph(s)
+    auto sort_counts = [&](uint32_t ca, uint32_t cb, int ph, uint32_t &lo, uint32_t &hi) {
+        const uint32_t sl = ph == 0 ? 0x3210u : ph == 1 ? 0x6420u : 0x5140u;
+        const uint32_t sh = ph == 0 ? 0x7654u : ph == 1 ? 0x7531u : 0x7362u;
+        lo += prmt(ca, cb, sl);
+        hi += prmt(ca, cb, sh);
+    };
+    auto add_totals = [&](uint32_t lo, uint32_t hi) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            tot[s] += (lo >> (8 * s)) & 0xFFu;
+            tot[s + 4] += (hi >> (8 * s)) & 0xFFu;
+        }
+    };
+    issue(0);
+    cp_async_commit();
+    for (uint32_t t = 0; t < ntiles; ++t) {
+        cp_async_wait<0>();
+        __syncwarp();
+        uint32_t w[32];
+        {
+            const uint8_t *srow = stage_ptr + lane * kTile;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((q ^ (lane & 7)) * 16));
+                w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+            }
+        }
+        __syncwarp();   // every lane holds its row: the stage can be refilled
+        if (t + 1 < ntiles) issue(t + 1);
+        cp_async_commit();
+        const uint64_t ro = pb + (uint64_t)t * kTile;
+        if (!(ro + kTile > from && ro < to)) continue;   // no byte of this row is in the part
+        const bool full = ro >= from && ro + kTile <= to;
+        bool done = false;
+        if (full) {
+            const uint32_t R0 = R;
+            uint32_t ca[3] = {0, 0, 0}, cb[3] = {0, 0, 0}, err = 0;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const uint32_t x = w[k] & 0x06060606u;
+                const uint32_t y = mad_lo(x, k65, 0u);   // pair codes at bits 7..10 and 23..26
+                const uint2 r1 = lds_v2(tab2_addr + (__umulhi(y, h28) & 0x78u));
+                const uint2 r2 = lds_v2(tab2_addr + (__umulhi(y, h12) & 0x78u));
+                uint32_t a, bb;
+                step(R, r1, a, bb);
+                ca[(2 * k) % 3] = mad_lo(a, k1, ca[(2 * k) % 3]);
+                cb[(2 * k) % 3] = mad_lo(bb, k1, cb[(2 * k) % 3]);
+                step(R, r2, a, bb);
+                ca[(2 * k + 1) % 3] = mad_lo(a, k1, ca[(2 * k + 1) % 3]);
+                cb[(2 * k + 1) % 3] = mad_lo(bb, k1, cb[(2 * k + 1) % 3]);
+                // bit-exact base check: expected lowercase bytes selected by the codes
+                const uint32_t z = mad_lo(__umulhi(x, h28), k1, x);   // x | x >> 4 (no common bits)
+                err |= prmt(p.lut_lo, p.lut_hi, prmt(z, 0u, 0x0020u)) ^ w[k];
+            }
+            if ((err & 0xDFDFDFDFu) == 0) {
+                // 64 steps: the run from s sits in field rotl3(s); two identity steps
+                // bring every run back to its own field
+                uint32_t u0, u1;
+                step(R, ident, u0, u1);
+                step(R, ident, u0, u1);
+                uint32_t lo = 0, hi = 0;
+                sort_counts(ca[0], cb[0], 0, lo, hi);
+                sort_counts(ca[1], cb[1], 1, lo, hi);
+                sort_counts(ca[2], cb[2], 2, lo, hi);
+                add_totals(lo, hi);
+                done = true;
+            } else {
+                R = R0;
+            }
+        }
+        if (!done) {
+            // reset bytes or a part edge in this row: one symbol per step, every run
+            // brought back to its own field after each
+            const uint32_t k0 = ro < from ? (uint32_t)(from - ro) : 0u;
+            const uint32_t kn = ro + kTile > to ? (uint32_t)(to - ro) : (uint32_t)kTile;
+            uint32_t lo = 0, hi = 0;
+            for (uint32_t k = k0; k < kn; ++k) {
+                const uint32_t byte = p.abase[ro + k];   // the row is in L2
+                const uint32_t code = byte_is_base(byte) ? ((byte >> 1) & 3u) : 4u;
+                uint32_t a, bb, u0, u1;
+                step(R, tab1[code], a, bb);
+                lo += a;
+                hi += bb;
+                step(R, ident, u0, u1);
+                step(R, ident, u0, u1);
+            }
+            add_totals(lo, hi);
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    // prefix composition of the warp's 32 part maps, then of the block's chunk maps: the
+    // join sees one map per block, and (positions pass) each chunk's start per block start
+    uint32_t e[8], cn[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { e[s] = (R >> (4 * s)) & 15u; cn[s] = tot[s]; }
+    compose_prefix(e, cn, reinterpret_cast<uint32_t *>(stage_ptr) + lane * 17, lane);
+    if (p.bound && c < p.n_chunks) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const uint32_t xe = __shfl_up_sync(0xFFFFFFFFu, e[s], 1);
+            p.bound[((uint64_t)c * 32u + lane) * 32u + s] = lane ? xe : (uint32_t)s;
+        }
+    }
+    __shared__ uint32_t chunk_map[kNibWarps][16];
+    if (lane == 31) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) { chunk_map[warp][s] = e[s]; chunk_map[warp][8 + s] = cn[s]; }
+    }
+    __syncthreads();
+    if (warp != 0) return;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        e[s] = lane < kNibWarps ? chunk_map[lane][s] : (uint32_t)s;
+        cn[s] = lane < kNibWarps ? chunk_map[lane][8 + s] : 0u;
+    }
+    compose_prefix(e, cn, reinterpret_cast<uint32_t *>(stage_ptr) + lane * 17, lane);
+    const uint32_t cl = blockIdx.x * kNibWarps + (uint32_t)lane;   // the lane's chunk
+    uint32_t xe[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) xe[s] = __shfl_up_sync(0xFFFFFFFFu, e[s], 1);
+    if (p.cpre && lane < kNibWarps && cl < p.n_chunks) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) p.cpre[(uint64_t)cl * 8u + s] = lane ? xe[s] : (uint32_t)s;
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            p.map_end[(uint64_t)blockIdx.x * 32u + s] = e[s];
+            p.map_cnt[(uint64_t)blockIdx.x * 32u + s] = cn[s];
+        }
+    }
+}
+
 struct JoinParams {
     const uint32_t *map_end, *map_cnt, *bound, *gstart;
     uint32_t n_chunks;
@@ -334,6 +616,10 @@ struct JoinParams {
     uint32_t qp;                // row width of the map arrays (32 * warps per chunk)
     uint32_t parts;             // G of the map kernel: parts per chunk
     uint32_t *given;            // [n_chunks * 32] exact start of each sub-chunk, or null
+    // map_nib_kernel: the maps are per block of 'chunk_block' chunks (n_chunks counts the
+    // blocks); cpre gives each chunk's start per block start state; else null
+    const uint32_t *cpre;
+    uint32_t *bstart;           // (with cpre) receives each block's start state
     uint64_t *out_count;
     uint32_t start;             // the state the sequence starts in
     uint32_t *out_last;         // null, or receives the state after the last byte
@@ -355,16 +641,27 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
     uint32_t *g_end = jsm;                      // [ng][qp]
     uint32_t *g_cnt = g_end + ng * qp;          // [ng][qp]
     uint32_t *g_start = g_cnt + ng * qp;        // [ng]
-    uint32_t *wbuf = g_start + ng;              // per warp (maps 32 wide): [32 chunks][32] ends, then counts
+    // per warp (maps 32 wide): [32 chunks][32] ends, then counts; 16-byte aligned
+    uint32_t *wbuf = g_start + ((ng + 3u) & ~3u);
     uint32_t *my_end = wbuf + (size_t)warp * 2048;
     uint32_t *my_cnt = my_end + 1024;
+    uint32_t *kst = wbuf + (size_t)kJoinWarps * 2048 + (size_t)warp * 32;   // [32] chunk starts
     auto group_size = [&](uint32_t g) { return p.n_chunks - g * 32 < 32 ? p.n_chunks - g * 32 : 32u; };
+    // a group's maps (nk x 32 words each) into shared memory: every 16-byte copy is issued
+    // before the first is waited for
     auto load_group = [&](uint32_t g) {
         const uint32_t nk = group_size(g);
-        for (uint32_t i = lane; i < nk * 32; i += 32) {
-            my_end[i] = p.map_end[(uint64_t)g * 1024 + i];
-            my_cnt[i] = p.map_cnt[(uint64_t)g * 1024 + i];
+        const uint32_t e0 = (uint32_t)__cvta_generic_to_shared(my_end), c0 = (uint32_t)__cvta_generic_to_shared(my_cnt);
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t i = (j * 32u + (uint32_t)lane) * 4u;   // word index of this 16-byte piece
+            if (i < nk * 32u) {
+                cp_async16(e0 + i * 4u, p.map_end + (uint64_t)g * 1024 + i, 16u);
+                cp_async16(c0 + i * 4u, p.map_cnt + (uint64_t)g * 1024 + i, 16u);
+            }
         }
+        cp_async_commit();
+        cp_async_wait<0>();
         __syncwarp();
         return nk;
     };
@@ -410,18 +707,54 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 1) map_join_kernel(JoinParams
     if (!p.given) return;
     for (uint32_t g = warp; g < ng; g += kJoinWarps) {
         const uint32_t nk = qp == 32 ? load_group(g) : group_size(g);
-        uint32_t s = g_start[g];
+        // the group's chunk starts (one lane walks the maps), then every sub-chunk's start
+        // with the loads of eight chunks in flight at once
+        if (p.cpre) {
+            // the maps are per block: each block's start goes out for nib_given_kernel,
+            // which gives every sub-chunk's start from it
+            if (lane == 0) {
+                uint32_t s = g_start[g];
+                for (uint32_t k = 0; k < nk; ++k) {
+                    p.bstart[(uint64_t)g * 32 + k] = s;
+                    s = my_end[k * 32 + s];
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        if (lane == 0) {
+            uint32_t s = g_start[g];
+            for (uint32_t k = 0; k < nk; ++k) {
+                kst[k] = s;
+                s = qp == 32 ? my_end[k * 32 + s] : p.map_end[((uint64_t)g * 32 + k) * qp + s];
+            }
+        }
+        __syncwarp();
         // sub-chunk 'lane' lies in part gl of its chunk; its recorded states are indexed
         // by the state at that part's start
         const uint32_t gl = (uint32_t)lane / (kMapSubs / p.parts);
+#pragma unroll 8
         for (uint32_t k = 0; k < nk; ++k) {
             const uint64_t c = (uint64_t)g * 32 + k;
+            const uint32_t s = kst[k];
             const uint32_t sp = gl ? p.gstart[(c * p.parts + gl) * 32u + s] : s;
             p.given[c * kMapSubs + lane] = p.bound[(c * kMapSubs + lane) * qp + sp];
-            s = qp == 32 ? my_end[k * 32 + s] : p.map_end[c * qp + s];
         }
         __syncwarp();
     }
+}
+
+// The positions pass's start of every sub-chunk of the nibble path (a part: 32 per
+// chunk): its chunk's start from the chunk's block start, then the part's start from
+// the chunk's start. One thread per sub-chunk.
+__global__ void nib_given_kernel(const uint32_t *bstart, const uint32_t *cpre, const uint32_t *bound,
+                                 uint32_t *given, uint32_t n_chunks) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (uint64_t)n_chunks * kMapSubs) return;
+    const uint64_t c = i / kMapSubs;
+    const uint32_t sb = bstart[c / kNibWarps];
+    const uint32_t sc = cpre[c * 8u + sb];
+    given[i] = bound[i * 32u + sc];
 }
 
 }  // namespace
@@ -446,10 +779,12 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     // one wave of warps: every chunk takes wblocks of them
     const uint64_t tasks = (uint64_t)(pr.sms ? pr.sms : 152) * kMapWarps;
     const uint64_t unit = (uint64_t)kMapSubs * kTile;                        // 4 KiB
-    // lane groups of 8, 16 or 32 start states; two chains per lane up to 32 states
-    const uint32_t groups = d->n_states <= 8 ? 4u : d->n_states <= 16 ? 2u : 1u;
+    // at most 8 states: every run of a part in one word, a lane per part (map_nib_kernel);
+    // else lane groups of 16 or 32 start states, two chains per lane up to 32 states
+    const bool nib = d->n_states <= 8;
+    const uint32_t groups = d->n_states <= 16 ? 2u : 1u;
     const uint32_t chains = d->n_states <= 32 ? 2u : 1u;
-    const uint32_t parts = groups * chains;
+    const uint32_t parts = nib ? 1u : groups * chains;
     const int tab = d->d_pair ? TAB_PAIR : TAB_ONE;
     const uint64_t want_chunks = std::max<uint64_t>(1, tasks / wblocks);
     uint64_t S = (total + want_chunks - 1) / want_chunks;
@@ -466,13 +801,16 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     const size_t o_bound = positions ? take(nq * kMapSubs * 4) : 0;
     const size_t o_gstart = positions ? take((size_t)n_chunks * 32 * parts * 4) : 0;
     const size_t o_given = positions ? take((size_t)n_chunks * kMapSubs * 4) : 0;
+    const size_t o_cpre = positions && nib ? take((size_t)n_chunks * 8 * 4) : 0;
+    const size_t o_bstart = positions && nib ? take((size_t)n_chunks * 4) : 0;
     const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
     const size_t part_tile = chains == 1 ? (size_t)kMapTile : (size_t)2048 / parts;
-    const size_t msmem = (size_t)kMapWarps * 2 * parts * part_tile + (size_t)d->n_states * 16 + 2048 +
-                         (size_t)d->n_states * (tab == TAB_PAIR ? (size_t)kPairRowBytes : (size_t)kOneRowBytes);
-    void (*fn)(MapParams) = tab == TAB_ONE ? map_kernel<1, TAB_ONE, 1>
+    const size_t msmem = nib ? (size_t)kNibWarps * kStageBytesNib
+                             : (size_t)kMapWarps * 2 * parts * part_tile + (size_t)d->n_states * 16 + 2048 +
+                                   (size_t)d->n_states * (tab == TAB_PAIR ? (size_t)kPairRowBytes : (size_t)kOneRowBytes);
+    void (*fn)(MapParams) = nib ? map_nib_kernel
+                          : tab == TAB_ONE ? map_kernel<1, TAB_ONE, 1>
                           : chains == 1 ? map_kernel<1, TAB_PAIR, 1>
-                          : groups == 4 ? map_kernel<4, TAB_PAIR, 2>
                           : groups == 2 ? map_kernel<2, TAB_PAIR, 2> : map_kernel<1, TAB_PAIR, 2>;
     // the kernel's static shared memory (its decoded rows, 3.5 KB per part) comes off the
     // block's shared memory before the dynamic part
@@ -484,7 +822,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     }
     if (static_smem + 1024 >= optin || msmem > optin - static_smem - 1024) return DNA_ERR_CAPACITY;
     const uint32_t ng = (n_chunks + 31) / 32;
-    const size_t jsmem = ((size_t)ng * (2 * qp + 1) + (qp == 32 ? (size_t)kJoinWarps * 2048 : 0)) * 4;
+    const size_t jsmem = ((size_t)ng * 2 * qp + ((ng + 3) & ~(size_t)3) + (size_t)kJoinWarps * (2048 + 32)) * 4;
     if (jsmem > optin - 1024) return DNA_ERR_CAPACITY;
     void *mem = nullptr;
     if (ext) {
@@ -503,20 +841,26 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     mp.map_end = (uint32_t *)(base + o_end); mp.map_cnt = (uint32_t *)(base + o_cnt);
     mp.bound = positions ? (uint32_t *)(base + o_bound) : nullptr;
     mp.gstart = positions && parts > 1 ? (uint32_t *)(base + o_gstart) : nullptr;
+    mp.cpre = positions && nib ? (uint32_t *)(base + o_cpre) : nullptr;
     mp.k1 = 1u; mp.k5 = 32u; mp.lut_lo = 0x00630061u; mp.lut_hi = 0x00670074u;
     int rc = ensure_smem_optin((const void *)fn, d->device, optin - static_smem - 1024);
     cudaError_t e = rc ? cudaErrorInvalidValue : cudaSuccess;
     if (e == cudaSuccess) {
         const uint64_t n_tasks = (uint64_t)n_chunks * wblocks;
         const ProfToken tk = prof_begin(stream);
-        fn<<<(unsigned)((n_tasks + kMapWarps - 1) / kMapWarps), kMapWarps * 32, msmem, stream>>>(mp);
+        const int warps = nib ? kNibWarps : kMapWarps;
+        fn<<<(unsigned)((n_tasks + warps - 1) / warps), warps * 32, msmem, stream>>>(mp);
         e = cudaGetLastError();
         prof_end(tk, stream, PROF_SCAN);
         record_launch();
     }
     JoinParams jp;
     jp.map_end = mp.map_end; jp.map_cnt = mp.map_cnt; jp.bound = mp.bound; jp.gstart = mp.gstart;
-    jp.n_chunks = n_chunks; jp.n_states = d->n_states; jp.qp = qp; jp.parts = parts;
+    // map_nib_kernel leaves one map per block of kNibWarps chunks
+    const uint32_t n_blocks_nib = (n_chunks + kNibWarps - 1) / kNibWarps;
+    jp.n_chunks = nib ? n_blocks_nib : n_chunks; jp.n_states = d->n_states; jp.qp = qp; jp.parts = parts;
+    jp.cpre = mp.cpre;
+    jp.bstart = positions && nib ? (uint32_t *)(base + o_bstart) : nullptr;
     jp.given = positions ? (uint32_t *)(base + o_given) : nullptr;
     jp.out_count = out_count;
     jp.start = from ? from->start : 0u;
@@ -528,6 +872,13 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     }
     if (e == cudaSuccess) {
         map_join_kernel<<<1, kJoinWarps * 32, jsmem, stream>>>(jp);
+        e = cudaGetLastError();
+        record_launch();
+    }
+    if (e == cudaSuccess && positions && nib) {
+        const uint64_t n_sub = (uint64_t)n_chunks * kMapSubs;
+        nib_given_kernel<<<(unsigned)((n_sub + 255) / 256), 256, 0, stream>>>(jp.bstart, jp.cpre, jp.bound,
+                                                                               jp.given, n_chunks);
         e = cudaGetLastError();
         record_launch();
     }
