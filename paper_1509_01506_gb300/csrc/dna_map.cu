@@ -336,19 +336,20 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
 // A lane walks one part of the chunk (a warp's 32 lanes walk its 32 parts, which are also
 // the positions pass's sub-chunks) and follows every start state at once: the state of
 // the run from each start sits in a 4-bit field of one register. A two-symbol step looks
-// up the pair's 8-byte row (byte j: the state two symbols after state j, and the
-// accepting steps on the way, << 4) and moves every run through it with two byte
-// permutes: permute(row, fields 0..3) gives the new states of fields 0..3 as bytes, and
-// permute(row, fields 4..7) those of fields 4..7, which are packed back as
-// (fields 0..3 bytes) | (fields 4..7 bytes << 4). The packing moves the run in field i
-// to field rotl3(i) (i = 0..3 go to 0, 2, 4, 6 and i = 4..7 to 1, 3, 5, 7), a
-// permutation of period 3, so a row starts with field s holding the run from s and the
-// step number mod 3 tells where each run is; the count bytes of each step are kept per
-// step number mod 3 and sorted back to runs at the end of the row. The 16 rows of the
-// pair table fill one 128-byte line, so the lanes' lookups never conflict in shared
-// memory. The warp then composes its 32 part maps with a prefix scan: the last lane's
-// result is the chunk map, and every lane's exclusive prefix is the state at its part's
-// start for each chunk start state (the positions pass's sub-chunk starts).
+// up the pair's row (8 state bytes: the state two symbols after state j; 8 count bytes:
+// the accepting steps on the way; the state rows and the count rows of the 16 pairs are
+// two 128-byte tables, so the lanes' 8-byte lookups never conflict in shared memory) and
+// moves every run through it with byte permutes: permute(states, fields 0..3) gives the new states of fields 0..3 as bytes,
+// and permute(states, fields 4..7) those of fields 4..7, packed back as (fields 0..3
+// bytes) + (fields 4..7 bytes) x 16; the same permutes of the count bytes give each run's
+// accepting steps. The packing moves the run in field i to field rotl3(i) (i = 0..3 go to
+// 0, 2, 4, 6 and i = 4..7 to 1, 3, 5, 7), a permutation of period 3, so a row starts with
+// field s holding the run from s and the step number mod 3 tells where each run is; the
+// count bytes are kept per step number mod 3 and sorted back to runs at the end of the
+// row. The warp then composes its 32 part maps with a prefix scan (every lane's exclusive
+// prefix is the state at its part's start for each chunk start state: the positions
+// pass's sub-chunk starts), and the block composes its chunks' maps the same way, so the
+// join sees one map per block.
 constexpr int kNibWarps = 24;
 constexpr uint32_t kStageBytesNib = 32u * kTile;   // one 128-byte row of each of 32 parts
 
@@ -364,6 +365,7 @@ __device__ __forceinline__ uint2 lds_v2(uint32_t addr) {
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
     return v;
 }
+
 
 // Inclusive prefix composition across the lanes of a warp (Kogge-Stone): lane i holds
 // the map of item i (e: end state per start state, cn: accepting steps per start state)
@@ -394,35 +396,43 @@ __device__ __forceinline__ void compose_prefix(uint32_t (&e)[8], uint32_t (&cn)[
 
 __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ __align__(128) uint2 tab2[16];   // pair rows, pair index = code1 + 4 x code2
-    __shared__ __align__(8) uint2 tab1[5];      // one-symbol rows, index code (4: a reset byte)
+    __shared__ __align__(128) uint2 tab2s[16];  // pair rows, states; pair = code1 + 4 x code2
+    __shared__ __align__(128) uint2 tab2c[16];  // pair rows, accepting steps
+    __shared__ __align__(16) uint4 tab1[5];     // one-symbol rows, index code (4: a reset byte)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t Q = p.n_states;
-    // byte j of a row: next state | accepting steps << 4; fields past n_states stay put
+    // byte j of a row: next state of state j (bytes 0..7), accepting steps (bytes 8..15);
+    // fields past n_states stay put
     if (threadIdx.x < 21) {
         const uint32_t i = threadIdx.x;
-        uint32_t lo = 0, hi = 0;
+        uint32_t st[2] = {0, 0}, ct[2] = {0, 0};
         for (uint32_t j = 0; j < 8; ++j) {
-            uint32_t v = j;
+            uint32_t v = j, a = 0;
             if (j < Q) {
                 if (i < 16) {
                     const uint32_t e1 = p.one[j * 4u + (i & 3u)];
-                    const uint32_t q1 = e1 & 0x7FFFFFFFu;
-                    const uint32_t e2 = p.one[q1 * 4u + (i >> 2)];
-                    v = (e2 & 0x7FFFFFFFu) | (((e1 >> 31) + (e2 >> 31)) << 4);
+                    const uint32_t e2 = p.one[(e1 & 0x7FFFFFFFu) * 4u + (i >> 2)];
+                    v = e2 & 0x7FFFFFFFu;
+                    a = (e1 >> 31) + (e2 >> 31);
                 } else if (i < 20) {
                     const uint32_t e1 = p.one[j * 4u + (i - 16u)];
-                    v = (e1 & 0x7FFFFFFFu) | ((e1 >> 31) << 4);
+                    v = e1 & 0x7FFFFFFFu;
+                    a = e1 >> 31;
                 } else {
-                    v = (p.reset_entry >> 31) << 4;   // a reset: q0 (and whether it accepts)
+                    v = 0;                       // a reset: q0, counted when q0 accepts
+                    a = p.reset_entry >> 31;
                 }
             }
-            if (j < 4) lo |= v << (8 * j);
-            else hi |= v << (8 * (j - 4));
+            st[j >> 2] |= v << (8 * (j & 3u));
+            ct[j >> 2] |= a << (8 * (j & 3u));
         }
-        if (i < 16) tab2[i] = make_uint2(lo, hi);
-        else tab1[i - 16] = make_uint2(lo, hi);
+        if (i < 16) {
+            tab2s[i] = make_uint2(st[0], st[1]);
+            tab2c[i] = make_uint2(ct[0], ct[1]);
+        } else {
+            tab1[i - 16] = make_uint4(st[0], st[1], ct[0], ct[1]);
+        }
     }
     __syncthreads();
     // warps past the last chunk walk nothing (identity maps) and join the block's
@@ -431,7 +441,8 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
     uint8_t *stage_ptr = smem + (size_t)warp * kStageBytesNib;
     const uint32_t stage_addr = smem_base + (uint32_t)warp * kStageBytesNib;
-    const uint32_t tab2_addr = (uint32_t)__cvta_generic_to_shared(tab2);
+    const uint32_t tab2s_addr = (uint32_t)__cvta_generic_to_shared(tab2s);
+    const uint32_t tab2c_addr = (uint32_t)__cvta_generic_to_shared(tab2c);
     const uint64_t b = (uint64_t)c * p.chunk_bytes;
     const uint64_t part = p.chunk_bytes / 32u;          // multiple of kTile
     const uint64_t pb = b + (uint64_t)lane * part;
@@ -442,7 +453,8 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
     // run-time constants: the multiplies and high multiplies that use them (shifts) stay
     // on the multiply-add pipe, beside the byte permutes and logic on the integer pipe
     const uint32_t k1 = p.k1, k16 = p.k5 >> 1, k65 = p.k1 * 65u;
-    const uint32_t h16 = p.k5 << 11, h28 = p.k5 << 23, h12 = p.k5 << 7;   // x >> 16, >> 4, >> 20
+    const uint32_t h16 = p.k5 << 11, h28 = p.k5 << 23;    // high multiplies: x >> 16, x >> 4
+    const uint32_t h12 = p.k5 << 7;                      // x >> 20
     // staging: tile t of the 32 parts into a swizzled [32 rows][128 B] stage (16-byte
     // column c of row r at slot c ^ (r & 7)); copy j of a lane moves column lane & 7 of
     // row 4j + lane / 8, so each copy instruction covers four whole 128-byte lines
@@ -456,19 +468,21 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             cp_async16(stage_addr + r * kTile + ((cc ^ (r & 7u)) << 4), ok ? p.abase + off : p.abase, ok ? 16u : 0u);
         }
     };
-    // one step of every run: fields 0..3 and 4..7 through the row (lo, hi); returns the
-    // count bytes of fields 0..3 (ca) and 4..7 (cb)
-    auto step = [&](uint32_t &R, uint2 row, uint32_t &ca, uint32_t &cb) {
-        const uint32_t A = prmt(row.x, row.y, R);
-        const uint32_t B = prmt(row.x, row.y, __umulhi(R, h16));
-        const uint32_t B16 = mad_lo(B, k16, 0u);
-        uint32_t r;   // (A & 0x07070707) | (B16 & ~0x07070707), one lop3
-        asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(r) : "r"(A), "r"(B16), "r"(0x07070707u));
-        R = r;
-        ca = __umulhi(A, h28) & 0x03030303u;
-        cb = __umulhi(B, h28) & 0x03030303u;
+    // one step of every run through a row: the count bytes of fields 0..3 and 4..7 are
+    // added to ca and cb
+    auto step = [&](uint32_t &R, uint2 rs, uint2 rc, uint32_t &ca, uint32_t &cb) {
+        const uint32_t Rh = __umulhi(R, h16);   // fields 4..7
+        const uint32_t A = prmt(rs.x, rs.y, R), B = prmt(rs.x, rs.y, Rh);
+        ca = mad_lo(prmt(rc.x, rc.y, R), k1, ca);
+        cb = mad_lo(prmt(rc.x, rc.y, Rh), k1, cb);
+        R = mad_lo(B, k16, A);   // the bytes hold 3-bit states: B x 16 and A share no bit
     };
-    const uint2 ident = make_uint2(0x03020100u, 0x07060504u);
+    // the identity step (no counts): moves every run as a step does
+    auto shuffle = [&](uint32_t &R) {
+        const uint32_t A = prmt(0x03020100u, 0x07060504u, R);
+        const uint32_t B = prmt(0x03020100u, 0x07060504u, __umulhi(R, h16));
+        R = mad_lo(B, k16, A);
+    };
     uint32_t R = 0x76543210u;   // field s: the run from start state s
     uint32_t tot[8];
 #pragma unroll
@@ -516,15 +530,10 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             for (int k = 0; k < 32; ++k) {
                 const uint32_t x = w[k] & 0x06060606u;
                 const uint32_t y = mad_lo(x, k65, 0u);   // pair codes at bits 7..10 and 23..26
-                const uint2 r1 = lds_v2(tab2_addr + (__umulhi(y, h28) & 0x78u));
-                const uint2 r2 = lds_v2(tab2_addr + (__umulhi(y, h12) & 0x78u));
-                uint32_t a, bb;
-                step(R, r1, a, bb);
-                ca[(2 * k) % 3] = mad_lo(a, k1, ca[(2 * k) % 3]);
-                cb[(2 * k) % 3] = mad_lo(bb, k1, cb[(2 * k) % 3]);
-                step(R, r2, a, bb);
-                ca[(2 * k + 1) % 3] = mad_lo(a, k1, ca[(2 * k + 1) % 3]);
-                cb[(2 * k + 1) % 3] = mad_lo(bb, k1, cb[(2 * k + 1) % 3]);
+                // 8-byte rows: pair x 8 from bits 7..10 (and 23..26) of y
+                const uint32_t o1 = __umulhi(y, h28) & 0x78u, o2 = __umulhi(y, h12) & 0x78u;
+                step(R, lds_v2(tab2s_addr + o1), lds_v2(tab2c_addr + o1), ca[(2 * k) % 3], cb[(2 * k) % 3]);
+                step(R, lds_v2(tab2s_addr + o2), lds_v2(tab2c_addr + o2), ca[(2 * k + 1) % 3], cb[(2 * k + 1) % 3]);
                 // bit-exact base check: expected lowercase bytes selected by the codes
                 const uint32_t z = mad_lo(__umulhi(x, h28), k1, x);   // x | x >> 4 (no common bits)
                 err |= prmt(p.lut_lo, p.lut_hi, prmt(z, 0u, 0x0020u)) ^ w[k];
@@ -532,9 +541,8 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             if ((err & 0xDFDFDFDFu) == 0) {
                 // 64 steps: the run from s sits in field rotl3(s); two identity steps
                 // bring every run back to its own field
-                uint32_t u0, u1;
-                step(R, ident, u0, u1);
-                step(R, ident, u0, u1);
+                shuffle(R);
+                shuffle(R);
                 uint32_t lo = 0, hi = 0;
                 sort_counts(ca[0], cb[0], 0, lo, hi);
                 sort_counts(ca[1], cb[1], 1, lo, hi);
@@ -554,12 +562,10 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             for (uint32_t k = k0; k < kn; ++k) {
                 const uint32_t byte = p.abase[ro + k];   // the row is in L2
                 const uint32_t code = byte_is_base(byte) ? ((byte >> 1) & 3u) : 4u;
-                uint32_t a, bb, u0, u1;
-                step(R, tab1[code], a, bb);
-                lo += a;
-                hi += bb;
-                step(R, ident, u0, u1);
-                step(R, ident, u0, u1);
+                const uint4 r = tab1[code];
+                step(R, make_uint2(r.x, r.y), make_uint2(r.z, r.w), lo, hi);
+                shuffle(R);
+                shuffle(R);
             }
             add_totals(lo, hi);
         }
@@ -777,7 +783,7 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     const uint32_t wblocks = (d->n_states + 31) / 32;
     const uint32_t qp = 32 * wblocks;
     // one wave of warps: every chunk takes wblocks of them
-    const uint64_t tasks = (uint64_t)(pr.sms ? pr.sms : 152) * kMapWarps;
+    const uint64_t tasks = (uint64_t)(pr.sms ? pr.sms : 152) * (d->n_states <= 8 ? kNibWarps : kMapWarps);
     const uint64_t unit = (uint64_t)kMapSubs * kTile;                        // 4 KiB
     // at most 8 states: every run of a part in one word, a lane per part (map_nib_kernel);
     // else lane groups of 16 or 32 start states, two chains per lane up to 32 states
