@@ -554,7 +554,7 @@ def bench_plain_configs(dna, torch, stream, peak):
         "bytes": int(full.size), "ms_per_step": ms, "gbs": full.size / (ms * 1e-3) / 1e9,
         "matches": int(cnt.item()), "chunk_maps": bool(dfa.info().chunk_maps), "output": "count",
         "note": "runs from different states never meet: every chunk is run from all 8 states, "
-                "as 4 parts walked side by side"}
+                "held as 4-bit fields of one register per lane and moved by byte permutes"}
     # 64 states whose runs never meet: two warps per chunk, one per block of 32 start states
     rng = np.random.Generator(np.random.PCG64(64))
     table = np.stack([rng.permutation(64) for _ in range(4)], axis=1).astype(np.uint32)
