@@ -343,6 +343,70 @@ def test_chunk_maps_forced_on_a_converging_regex():
     check("regex", synth.CONFIG2_REGEX, seq, offset=0, plan=dict(placement=4), positions=False)
 
 
+def _reset_heavy(seed, n, frac):
+    """Noisy Markov bases with short N runs covering about 'frac' of the bytes, so that
+    most 128-byte rows hold a reset byte."""
+    s = synth.markov2(seed, n)
+    synth.overlay_runs(s, seed, 0.1, 40.0, "lower")
+    synth.overlay_runs(s, seed + 1, frac, 6.0, "N")
+    return s
+
+
+@pytest.mark.parametrize("Q", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("n,offset", [(1, 3), (127, 0), (129, 5), (32 * 4096 - 1, 7), (32 * 4096 + 1, 1),
+                                      (1 * MiB + 5, 11), (9 * MiB + 77, 2)])
+def test_nibble_chunk_maps_every_state_count(Q, n, offset):
+    """Automata of at most 8 states whose runs never meet keep every run of a part in
+    4-bit fields of one register. Every state count, an accepting start state, lengths
+    at part and row edges and unaligned starts: counts and positions equal the
+    oracle's."""
+    rng = np.random.default_rng(700 + Q)
+    table = np.stack([rng.permutation(Q) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = (rng.random(Q) < 0.4).astype(np.uint8)
+    acc[0] = 1
+    seq = noisy_markov(701 + n % 89, n) if n > 1000 else synth.uniform(702, n)
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    assert dfa.info().chunk_maps
+    c, p = gpu_run(dfa, to_device(seq, offset), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
+    c2, _ = gpu_run(dfa, to_device(seq, offset), positions=False)
+    assert c2 == want_c
+
+
+@pytest.mark.parametrize("frac", [0.3, 0.6, 1.0])
+def test_nibble_chunk_maps_with_reset_bytes_in_most_rows(frac):
+    """Rows with a reset byte take the one-symbol steps of the nibble kernel (every run
+    back to q0, counted when q0 accepts); an all-N sequence resets every byte."""
+    table, acc = _permutation_automaton(8, 711)
+    acc[0] = 1
+    n = 3 * MiB + 1234
+    seq = np.full(n, ord("N"), dtype=np.uint8) if frac == 1.0 else _reset_heavy(712, n, frac)
+    want_c, want_p = oracle.run(table.astype(np.int32), acc, seq)
+    dfa = dna.Dfa(table, dna.pack_accept(acc))
+    c, p = gpu_run(dfa, to_device(seq, 3), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
+
+
+def test_nibble_chunk_maps_on_a_counter_and_on_forced_small_regexes():
+    """A counter automaton (the number of A's mod 8: one symbol permutes, the others
+    keep the state), and small regexes whose runs do converge scanned through the
+    nibble chunk maps by request: results equal the oracle's."""
+    t = np.array([[(q + 1) % 8, q, q, q] for q in range(8)], dtype=np.uint32)
+    a = np.zeros(8, dtype=np.uint8)
+    a[0] = 1
+    seq = noisy_markov(720, 5 * MiB + 17)
+    want_c, want_p = oracle.run(t.astype(np.int32), a, seq)
+    dfa = dna.Dfa(t, dna.pack_accept(a))
+    assert dfa.info().chunk_maps
+    c, p = gpu_run(dfa, to_device(seq, 6), capacity=want_c + 3)
+    assert c == want_c and np.array_equal(p, want_p)
+    for pat in ("ACGT", "A(C|G)T", "TATAAA"):
+        assert dna.Dfa.from_regex(pat).info().n_states <= 8
+        check("regex", pat, seq, offset=1, plan=dict(placement=4))
+        check("regex", pat, seq, offset=0, plan=dict(placement=4), positions=False)
+
+
 def test_chunk_maps_full_size():
     """64 MiB against an 8-state permutation automaton (never converging)."""
     table, acc = _permutation_automaton(8, 77)
