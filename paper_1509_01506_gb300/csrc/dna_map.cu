@@ -5,12 +5,12 @@
 // on DNA (permutation-like tables, counters): there every chunk's repair walks the whole
 // chunk and every join cascades, serially. For those the scan follows the paper's
 // possible-starting-state approach in full (Sec. III-A): a chunk is run from every state
-// at once. Automata of at most 8 states keep all 8 runs of a lane in one register
+// at once. Automata of at most 16 states keep all runs of a lane in one or two registers
 // (map_nib_kernel below: a lane walks one of the chunk's 32 parts). Larger ones: a warp
 // runs one chunk from 32 start states (lane q from state 32w + q for the warp's state
 // block w); automata of more than 32 states give each chunk ceil(Q / 32) warps, and
-// automata of at most 16 states cut the chunk into 2 parts walked side by side by lane
-// groups, whose maps the warp composes. Each chunk yields a map (end
+// automata of at most 32 states cut the chunk into 2 parts walked side by side (two
+// chains per lane), whose maps the warp composes. Each chunk yields a map (end
 // state and count per start state) and, for the positions pass, the state at each of its
 // 32 sub-chunk boundaries per start state. A single-block join composes the maps in order
 // (chunk c starts in the end state of chunk c-1 from its true start), which gives the
@@ -64,7 +64,7 @@ struct MapParams {
                                 //   (null for a count-only scan)
     uint32_t *gstart;           // [n_chunks][G][32]: state at the start of part g per chunk start
                                 //   state (G > 1; null for a count-only scan)
-    uint32_t *cpre;             // map_nib_kernel, positions pass: [n_chunks][8] state at each
+    uint32_t *cpre;             // map_nib_kernel, positions pass: [n_chunks][16] state at each
                                 //   chunk's start per start state of its block (else null)
     uint32_t k1, k5, lut_lo, lut_hi;
 };
@@ -331,32 +331,50 @@ __global__ void __launch_bounds__(kMapWarps * 32, 1) map_kernel(MapParams p) {
     }
 }
 
-// ---- Automata of at most 8 states: the runs from all 8 start states as one word.
+// ---- Automata of at most 16 states: the runs from all start states in one or two words.
 //
 // A lane walks one part of the chunk (a warp's 32 lanes walk its 32 parts, which are also
 // the positions pass's sub-chunks) and follows every start state at once: the state of
-// the run from each start sits in a 4-bit field of one register. A two-symbol step looks
-// up the pair's row (8 state bytes: the state two symbols after state j; 8 count bytes:
-// the accepting steps on the way; the state rows and the count rows of the 16 pairs are
-// two 128-byte tables, so the lanes' 8-byte lookups never conflict in shared memory) and
-// moves every run through it with byte permutes: permute(states, fields 0..3) gives the new states of fields 0..3 as bytes,
-// and permute(states, fields 4..7) those of fields 4..7, packed back as (fields 0..3
-// bytes) + (fields 4..7 bytes) x 16; the same permutes of the count bytes give each run's
-// accepting steps. The packing moves the run in field i to field rotl3(i) (i = 0..3 go to
-// 0, 2, 4, 6 and i = 4..7 to 1, 3, 5, 7), a permutation of period 3, so a row starts with
-// field s holding the run from s and the step number mod 3 tells where each run is; the
-// count bytes are kept per step number mod 3 and sorted back to runs at the end of the
-// row. The warp then composes its 32 part maps with a prefix scan (every lane's exclusive
-// prefix is the state at its part's start for each chunk start state: the positions
-// pass's sub-chunk starts), and the block composes its chunks' maps the same way, so the
-// join sees one map per block.
+// the run from each start sits in a 4-bit field, 8 runs to a register (W registers for
+// up to 8 W states). A two-symbol step looks up the pair's rows (the state two symbols
+// after state j, and the accepting steps on the way, as bytes; 8-byte rows, each kind a
+// 128-byte table of the 16 pairs, so the lanes' lookups never conflict in shared memory)
+// and moves every run through them with byte permutes: permute(row, fields 0..3) gives
+// the new states of fields 0..3 as bytes, and permute(row, fields 4..7) those of fields
+// 4..7, packed back as (fields 0..3 bytes) + (fields 4..7 bytes) x 16; the same permutes
+// of the count rows give each run's accepting steps. A permute selects one of 8 bytes by
+// the low 3 bits of a field and copies the byte's sign instead when the field's bit 3 is
+// set, so for 16 states (W = 2) each permute is taken from the rows of states 0..7 and of
+// states 8..15 with bit 3 cleared, and a permute of 0x80 bytes by the fields themselves
+// (0xFF where bit 3 is set, 0x80 where not) chooses between them bit by bit.
+// The packing moves the run in field i to field rotl3(i) (i = 0..3 go to 0, 2, 4, 6 and
+// i = 4..7 to 1, 3, 5, 7), a permutation of period 3, so a row starts with field i holding
+// the run from start 8r + i and the step number mod 3 tells where each run is; the count
+// bytes are kept per step number mod 3 and sorted back to runs at the end of the row.
+// At the end the lanes of a warp walk the 32 part maps in order (the chunk map, and every
+// part's start per chunk start state: the positions pass's sub-chunk starts), and the
+// first warp walks the block's chunk maps the same way, so the join sees one map per
+// block.
 constexpr int kNibWarps = 24;
 constexpr uint32_t kStageBytesNib = 32u * kTile;   // one 128-byte row of each of 32 parts
+constexpr uint32_t kNibMaxStates = 16;
+constexpr uint32_t kNibRow = 2u + kNibMaxStates + 1u;   // composition row: 2 end words, 16 counts, pad
+constexpr uint32_t kNibTotRow = kNibMaxStates + 1u;     // a lane's per-start totals (padded)
+// dynamic shared memory: the warps' stages, then every lane's per-start totals
+constexpr size_t kNibSmem = (size_t)kNibWarps * kStageBytesNib + (size_t)kNibWarps * 32 * kNibTotRow * 4;
 
-// byte permute with a selector whose fields never have bit 3 set (plain byte copies)
+// byte permute (prmt default mode)
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t d;
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// bitwise m ? b : a, one lop3: with inputs (b, a, m) the table of (b & m) | (a & ~m) is
+// (0xF0 & 0xAA) | (0xCC & 0x55) = 0xE4
+__device__ __forceinline__ uint32_t lop3_sel(uint32_t a, uint32_t b, uint32_t m) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(b), "r"(a), "r"(m));
     return d;
 }
 
@@ -366,57 +384,37 @@ __device__ __forceinline__ uint2 lds_v2(uint32_t addr) {
     return v;
 }
 
+// The rows of one step: states and counts for states 0..7 (and 8..15 when W = 2).
+template <int W>
+struct NibRows {
+    uint2 s[W], c[W];
+};
 
-// Inclusive prefix composition across the lanes of a warp (Kogge-Stone): lane i holds
-// the map of item i (e: end state per start state, cn: accepting steps per start state)
-// and ends with the composition of items 0..i. 'own' is this lane's 16-word scratch row
-// in shared memory (the lookups by state).
-__device__ __forceinline__ void compose_prefix(uint32_t (&e)[8], uint32_t (&cn)[8], uint32_t *own, int lane) {
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t pe_[8], pc_[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            pe_[s] = __shfl_up_sync(0xFFFFFFFFu, e[s], d);
-            pc_[s] = __shfl_up_sync(0xFFFFFFFFu, cn[s], d);
-            own[s] = e[s];
-            own[8 + s] = cn[s];
-        }
-        __syncwarp();
-        if (lane >= d) {
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const uint32_t m = pe_[s];
-                e[s] = own[m];
-                cn[s] = pc_[s] + own[8 + m];
-            }
-        }
-        __syncwarp();
-    }
-}
-
+template <int W>
 __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ __align__(128) uint2 tab2s[16];  // pair rows, states; pair = code1 + 4 x code2
-    __shared__ __align__(128) uint2 tab2c[16];  // pair rows, accepting steps
-    __shared__ __align__(16) uint4 tab1[5];     // one-symbol rows, index code (4: a reset byte)
+    // pair rows, pair index = code1 + 4 x code2: [W halves][16 pairs] of 8 bytes, states
+    // and counts; one-symbol rows, index code (4: a reset byte)
+    __shared__ __align__(128) uint2 tab2s[W][16], tab2c[W][16];
+    __shared__ __align__(16) uint2 tab1s[5][W], tab1c[5][W];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t Q = p.n_states;
-    // byte j of a row: next state of state j (bytes 0..7), accepting steps (bytes 8..15);
-    // fields past n_states stay put
-    if (threadIdx.x < 21) {
-        const uint32_t i = threadIdx.x;
+    // byte j of half h: next state of state 8h + j; fields past n_states stay put
+    if (threadIdx.x < 21u * W) {
+        const uint32_t i = threadIdx.x % 21u, h = threadIdx.x / 21u;
         uint32_t st[2] = {0, 0}, ct[2] = {0, 0};
         for (uint32_t j = 0; j < 8; ++j) {
-            uint32_t v = j, a = 0;
-            if (j < Q) {
+            const uint32_t q = 8u * h + j;
+            uint32_t v = q, a = 0;
+            if (q < Q) {
                 if (i < 16) {
-                    const uint32_t e1 = p.one[j * 4u + (i & 3u)];
+                    const uint32_t e1 = p.one[q * 4u + (i & 3u)];
                     const uint32_t e2 = p.one[(e1 & 0x7FFFFFFFu) * 4u + (i >> 2)];
                     v = e2 & 0x7FFFFFFFu;
                     a = (e1 >> 31) + (e2 >> 31);
                 } else if (i < 20) {
-                    const uint32_t e1 = p.one[j * 4u + (i - 16u)];
+                    const uint32_t e1 = p.one[q * 4u + (i - 16u)];
                     v = e1 & 0x7FFFFFFFu;
                     a = e1 >> 31;
                 } else {
@@ -428,10 +426,11 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             ct[j >> 2] |= a << (8 * (j & 3u));
         }
         if (i < 16) {
-            tab2s[i] = make_uint2(st[0], st[1]);
-            tab2c[i] = make_uint2(ct[0], ct[1]);
+            tab2s[h][i] = make_uint2(st[0], st[1]);
+            tab2c[h][i] = make_uint2(ct[0], ct[1]);
         } else {
-            tab1[i - 16] = make_uint4(st[0], st[1], ct[0], ct[1]);
+            tab1s[i - 16][h] = make_uint2(st[0], st[1]);
+            tab1c[i - 16][h] = make_uint2(ct[0], ct[1]);
         }
     }
     __syncthreads();
@@ -441,8 +440,8 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
     uint8_t *stage_ptr = smem + (size_t)warp * kStageBytesNib;
     const uint32_t stage_addr = smem_base + (uint32_t)warp * kStageBytesNib;
-    const uint32_t tab2s_addr = (uint32_t)__cvta_generic_to_shared(tab2s);
-    const uint32_t tab2c_addr = (uint32_t)__cvta_generic_to_shared(tab2c);
+    const uint32_t tab2s_addr = (uint32_t)__cvta_generic_to_shared(&tab2s[0][0]);
+    const uint32_t tab2c_addr = (uint32_t)__cvta_generic_to_shared(&tab2c[0][0]);
     const uint64_t b = (uint64_t)c * p.chunk_bytes;
     const uint64_t part = p.chunk_bytes / 32u;          // multiple of kTile
     const uint64_t pb = b + (uint64_t)lane * part;
@@ -468,38 +467,69 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             cp_async16(stage_addr + r * kTile + ((cc ^ (r & 7u)) << 4), ok ? p.abase + off : p.abase, ok ? 16u : 0u);
         }
     };
-    // one step of every run through a row: the count bytes of fields 0..3 and 4..7 are
-    // added to ca and cb
-    auto step = [&](uint32_t &R, uint2 rs, uint2 rc, uint32_t &ca, uint32_t &cb) {
-        const uint32_t Rh = __umulhi(R, h16);   // fields 4..7
-        const uint32_t A = prmt(rs.x, rs.y, R), B = prmt(rs.x, rs.y, Rh);
-        ca = mad_lo(prmt(rc.x, rc.y, R), k1, ca);
-        cb = mad_lo(prmt(rc.x, rc.y, Rh), k1, cb);
-        R = mad_lo(B, k16, A);   // the bytes hold 3-bit states: B x 16 and A share no bit
+    // four fields (the low 16 bits of 'sel') through a row: their new states (or counts)
+    // as bytes
+    auto look = [&](const uint2 *rows, uint32_t sel, uint32_t s7, uint32_t m) {
+        if constexpr (W == 1) {
+            return prmt(rows[0].x, rows[0].y, sel);
+        } else {
+            return lop3_sel(prmt(rows[0].x, rows[0].y, s7), prmt(rows[1].x, rows[1].y, s7), m);
+        }
+    };
+    // one step of every run: the count bytes of fields 0..3 and 4..7 of register r are
+    // added to ca[r] and cb[r]
+    auto step = [&](uint32_t (&R)[W], const NibRows<W> &rw, uint32_t (&ca)[W], uint32_t (&cb)[W]) {
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+            const uint32_t sa = R[r], sb = __umulhi(R[r], h16);   // fields 0..3, 4..7
+            uint32_t sa7 = sa, sb7 = sb, ma = 0, mb = 0;
+            if constexpr (W > 1) {
+                sa7 = sa & 0x7777u; sb7 = sb & 0x7777u;
+                ma = prmt(0x80808080u, 0x80808080u, sa);
+                mb = prmt(0x80808080u, 0x80808080u, sb);
+            }
+            const uint32_t A = look(rw.s, sa, sa7, ma), B = look(rw.s, sb, sb7, mb);
+            ca[r] = mad_lo(look(rw.c, sa, sa7, ma), k1, ca[r]);
+            cb[r] = mad_lo(look(rw.c, sb, sb7, mb), k1, cb[r]);
+            R[r] = mad_lo(B, k16, A);   // 4-bit states in the bytes: B x 16 and A share no bit
+        }
     };
     // the identity step (no counts): moves every run as a step does
-    auto shuffle = [&](uint32_t &R) {
-        const uint32_t A = prmt(0x03020100u, 0x07060504u, R);
-        const uint32_t B = prmt(0x03020100u, 0x07060504u, __umulhi(R, h16));
-        R = mad_lo(B, k16, A);
-    };
-    uint32_t R = 0x76543210u;   // field s: the run from start state s
-    uint32_t tot[8];
+    const uint2 id_rows[2] = {make_uint2(0x03020100u, 0x07060504u), make_uint2(0x0B0A0908u, 0x0F0E0D0Cu)};
+    auto shuffle = [&](uint32_t (&R)[W]) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) tot[s] = 0;
-    // count bytes of one phase (step number mod 3) -> per-run byte sums: run s sits in
-    // field rotl3^ph(s)
+        for (int r = 0; r < W; ++r) {
+            const uint32_t sa = R[r], sb = __umulhi(R[r], h16);
+            uint32_t sa7 = sa, sb7 = sb, ma = 0, mb = 0;
+            if constexpr (W > 1) {
+                sa7 = sa & 0x7777u; sb7 = sb & 0x7777u;
+                ma = prmt(0x80808080u, 0x80808080u, sa);
+                mb = prmt(0x80808080u, 0x80808080u, sb);
+            }
+            R[r] = mad_lo(look(id_rows, sb, sb7, mb), k16, look(id_rows, sa, sa7, ma));
+        }
+    };
+    uint32_t R[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) R[r] = 0x76543210u + 0x88888888u * (uint32_t)r;   // field i: start 8r + i
+    // per-start totals of this lane's part, added to once per row
+    uint32_t *tot = reinterpret_cast<uint32_t *>(smem + (size_t)kNibWarps * kStageBytesNib) +
+                    ((uint32_t)warp * 32u + (uint32_t)lane) * kNibTotRow;
+#pragma unroll
+    for (int s = 0; s < 8 * W; ++s) tot[s] = 0;
+    // count bytes of one phase (step number mod 3) -> per-run byte sums: the run from
+    // start 8r + s sits in field rotl3^ph(s) of register r
     auto sort_counts = [&](uint32_t ca, uint32_t cb, int ph, uint32_t &lo, uint32_t &hi) {
         const uint32_t sl = ph == 0 ? 0x3210u : ph == 1 ? 0x6420u : 0x5140u;
         const uint32_t sh = ph == 0 ? 0x7654u : ph == 1 ? 0x7531u : 0x7362u;
         lo += prmt(ca, cb, sl);
         hi += prmt(ca, cb, sh);
     };
-    auto add_totals = [&](uint32_t lo, uint32_t hi) {
+    auto add_totals = [&](int r, uint32_t lo, uint32_t hi) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            tot[s] += (lo >> (8 * s)) & 0xFFu;
-            tot[s + 4] += (hi >> (8 * s)) & 0xFFu;
+            tot[8 * r + s] += (lo >> (8 * s)) & 0xFFu;
+            tot[8 * r + s + 4] += (hi >> (8 * s)) & 0xFFu;
         }
     };
     issue(0);
@@ -524,33 +554,51 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
         const bool full = ro >= from && ro + kTile <= to;
         bool done = false;
         if (full) {
-            const uint32_t R0 = R;
-            uint32_t ca[3] = {0, 0, 0}, cb[3] = {0, 0, 0}, err = 0;
+            uint32_t R0[W];
+#pragma unroll
+            for (int r = 0; r < W; ++r) R0[r] = R[r];
+            uint32_t ca[3][W], cb[3][W], err = 0;
+#pragma unroll
+            for (int ph = 0; ph < 3; ++ph)
+#pragma unroll
+                for (int r = 0; r < W; ++r) { ca[ph][r] = 0; cb[ph][r] = 0; }
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const uint32_t x = w[k] & 0x06060606u;
                 const uint32_t y = mad_lo(x, k65, 0u);   // pair codes at bits 7..10 and 23..26
                 // 8-byte rows: pair x 8 from bits 7..10 (and 23..26) of y
                 const uint32_t o1 = __umulhi(y, h28) & 0x78u, o2 = __umulhi(y, h12) & 0x78u;
-                step(R, lds_v2(tab2s_addr + o1), lds_v2(tab2c_addr + o1), ca[(2 * k) % 3], cb[(2 * k) % 3]);
-                step(R, lds_v2(tab2s_addr + o2), lds_v2(tab2c_addr + o2), ca[(2 * k + 1) % 3], cb[(2 * k + 1) % 3]);
+                NibRows<W> r1, r2;
+#pragma unroll
+                for (int h = 0; h < W; ++h) {
+                    r1.s[h] = lds_v2(tab2s_addr + 128u * h + o1);
+                    r1.c[h] = lds_v2(tab2c_addr + 128u * h + o1);
+                    r2.s[h] = lds_v2(tab2s_addr + 128u * h + o2);
+                    r2.c[h] = lds_v2(tab2c_addr + 128u * h + o2);
+                }
+                step(R, r1, ca[(2 * k) % 3], cb[(2 * k) % 3]);
+                step(R, r2, ca[(2 * k + 1) % 3], cb[(2 * k + 1) % 3]);
                 // bit-exact base check: expected lowercase bytes selected by the codes
                 const uint32_t z = mad_lo(__umulhi(x, h28), k1, x);   // x | x >> 4 (no common bits)
                 err |= prmt(p.lut_lo, p.lut_hi, prmt(z, 0u, 0x0020u)) ^ w[k];
             }
             if ((err & 0xDFDFDFDFu) == 0) {
-                // 64 steps: the run from s sits in field rotl3(s); two identity steps
+                // 64 steps: the run in field s moved to field rotl3(s); two identity steps
                 // bring every run back to its own field
                 shuffle(R);
                 shuffle(R);
-                uint32_t lo = 0, hi = 0;
-                sort_counts(ca[0], cb[0], 0, lo, hi);
-                sort_counts(ca[1], cb[1], 1, lo, hi);
-                sort_counts(ca[2], cb[2], 2, lo, hi);
-                add_totals(lo, hi);
+#pragma unroll
+                for (int r = 0; r < W; ++r) {
+                    uint32_t lo = 0, hi = 0;
+                    sort_counts(ca[0][r], cb[0][r], 0, lo, hi);
+                    sort_counts(ca[1][r], cb[1][r], 1, lo, hi);
+                    sort_counts(ca[2][r], cb[2][r], 2, lo, hi);
+                    add_totals(r, lo, hi);
+                }
                 done = true;
             } else {
-                R = R0;
+#pragma unroll
+                for (int r = 0; r < W; ++r) R[r] = R0[r];
             }
         }
         if (!done) {
@@ -558,61 +606,64 @@ __global__ void __launch_bounds__(kNibWarps * 32, 1) map_nib_kernel(MapParams p)
             // brought back to its own field after each
             const uint32_t k0 = ro < from ? (uint32_t)(from - ro) : 0u;
             const uint32_t kn = ro + kTile > to ? (uint32_t)(to - ro) : (uint32_t)kTile;
-            uint32_t lo = 0, hi = 0;
+            uint32_t lo[W], hi[W];
+#pragma unroll
+            for (int r = 0; r < W; ++r) { lo[r] = 0; hi[r] = 0; }
             for (uint32_t k = k0; k < kn; ++k) {
                 const uint32_t byte = p.abase[ro + k];   // the row is in L2
                 const uint32_t code = byte_is_base(byte) ? ((byte >> 1) & 3u) : 4u;
-                const uint4 r = tab1[code];
-                step(R, make_uint2(r.x, r.y), make_uint2(r.z, r.w), lo, hi);
+                NibRows<W> rw;
+#pragma unroll
+                for (int h = 0; h < W; ++h) { rw.s[h] = tab1s[code][h]; rw.c[h] = tab1c[code][h]; }
+                step(R, rw, lo, hi);
                 shuffle(R);
                 shuffle(R);
             }
-            add_totals(lo, hi);
+#pragma unroll
+            for (int r = 0; r < W; ++r) add_totals(r, lo[r], hi[r]);
         }
     }
     cp_async_wait<0>();
     __syncwarp();
-    // prefix composition of the warp's 32 part maps, then of the block's chunk maps: the
-    // join sees one map per block, and (positions pass) each chunk's start per block start
-    uint32_t e[8], cn[8];
+    // the part's map (end state per start, packed 8 to a word, and counts) into a row of
+    // the stage; lane s < 8 W then walks the 32 part maps in order from start s
+    uint32_t *rows = reinterpret_cast<uint32_t *>(stage_ptr);
+    uint32_t *mine = rows + lane * kNibRow;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) { e[s] = (R >> (4 * s)) & 15u; cn[s] = tot[s]; }
-    compose_prefix(e, cn, reinterpret_cast<uint32_t *>(stage_ptr) + lane * 17, lane);
-    if (p.bound && c < p.n_chunks) {
+    for (int r = 0; r < W; ++r) mine[r] = R[r];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const uint32_t xe = __shfl_up_sync(0xFFFFFFFFu, e[s], 1);
-            p.bound[((uint64_t)c * 32u + lane) * 32u + s] = lane ? xe : (uint32_t)s;
+    for (int s = 0; s < 8 * W; ++s) mine[2 + s] = tot[s];
+    __syncwarp();
+    __shared__ uint32_t chunk_map[kNibWarps][kNibRow];
+    const bool walker = (uint32_t)lane < 8u * W;
+    if (walker) {
+        uint32_t st = (uint32_t)lane, cn = 0;
+        for (uint32_t k = 0; k < 32; ++k) {
+            if (p.bound && c < p.n_chunks) p.bound[((uint64_t)c * 32u + k) * 32u + lane] = st;
+            const uint32_t *mk = rows + k * kNibRow;
+            cn += mk[2 + st];
+            st = (mk[st >> 3] >> (4 * (st & 7u))) & 15u;
         }
-    }
-    __shared__ uint32_t chunk_map[kNibWarps][16];
-    if (lane == 31) {
+        // the chunk's map: end states packed into fields, counts
+        const uint32_t field = st << (4 * (lane & 7));
+        uint32_t packed = field;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) { chunk_map[warp][s] = e[s]; chunk_map[warp][8 + s] = cn[s]; }
+        for (int o = 1; o < 8; o <<= 1) packed |= __shfl_xor_sync((1u << (8 * W)) - 1u, packed, o, 8);
+        if ((lane & 7) == 0) chunk_map[warp][lane >> 3] = packed;
+        chunk_map[warp][2 + lane] = cn;
     }
     __syncthreads();
-    if (warp != 0) return;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        e[s] = lane < kNibWarps ? chunk_map[lane][s] : (uint32_t)s;
-        cn[s] = lane < kNibWarps ? chunk_map[lane][8 + s] : 0u;
+    if (warp != 0 || !walker) return;
+    // the block's chunks in order from block start s = lane
+    uint32_t st = (uint32_t)lane, cn = 0;
+    for (uint32_t k = 0; k < (uint32_t)kNibWarps; ++k) {
+        const uint32_t ck = blockIdx.x * kNibWarps + k;
+        if (p.cpre && ck < p.n_chunks) p.cpre[(uint64_t)ck * kNibMaxStates + lane] = st;
+        cn += chunk_map[k][2 + st];
+        st = (chunk_map[k][st >> 3] >> (4 * (st & 7u))) & 15u;
     }
-    compose_prefix(e, cn, reinterpret_cast<uint32_t *>(stage_ptr) + lane * 17, lane);
-    const uint32_t cl = blockIdx.x * kNibWarps + (uint32_t)lane;   // the lane's chunk
-    uint32_t xe[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) xe[s] = __shfl_up_sync(0xFFFFFFFFu, e[s], 1);
-    if (p.cpre && lane < kNibWarps && cl < p.n_chunks) {
-#pragma unroll
-        for (int s = 0; s < 8; ++s) p.cpre[(uint64_t)cl * 8u + s] = lane ? xe[s] : (uint32_t)s;
-    }
-    if (lane == 31) {
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            p.map_end[(uint64_t)blockIdx.x * 32u + s] = e[s];
-            p.map_cnt[(uint64_t)blockIdx.x * 32u + s] = cn[s];
-        }
-    }
+    p.map_end[(uint64_t)blockIdx.x * 32u + lane] = st;
+    p.map_cnt[(uint64_t)blockIdx.x * 32u + lane] = cn;
 }
 
 struct JoinParams {
@@ -622,7 +673,7 @@ struct JoinParams {
     uint32_t qp;                // row width of the map arrays (32 * warps per chunk)
     uint32_t parts;             // G of the map kernel: parts per chunk
     uint32_t *given;            // [n_chunks * 32] exact start of each sub-chunk, or null
-    // map_nib_kernel: the maps are per block of 'chunk_block' chunks (n_chunks counts the
+    // map_nib_kernel: the maps are per block of kNibWarps chunks (n_chunks counts the
     // blocks); cpre gives each chunk's start per block start state; else null
     const uint32_t *cpre;
     uint32_t *bstart;           // (with cpre) receives each block's start state
@@ -759,7 +810,7 @@ __global__ void nib_given_kernel(const uint32_t *bstart, const uint32_t *cpre, c
     if (i >= (uint64_t)n_chunks * kMapSubs) return;
     const uint64_t c = i / kMapSubs;
     const uint32_t sb = bstart[c / kNibWarps];
-    const uint32_t sc = cpre[c * 8u + sb];
+    const uint32_t sc = cpre[c * kNibMaxStates + sb];
     given[i] = bound[i * 32u + sc];
 }
 
@@ -783,12 +834,12 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     const uint32_t wblocks = (d->n_states + 31) / 32;
     const uint32_t qp = 32 * wblocks;
     // one wave of warps: every chunk takes wblocks of them
-    const uint64_t tasks = (uint64_t)(pr.sms ? pr.sms : 152) * (d->n_states <= 8 ? kNibWarps : kMapWarps);
+    const uint64_t tasks = (uint64_t)(pr.sms ? pr.sms : 152) * (d->n_states <= kNibMaxStates ? kNibWarps : kMapWarps);
     const uint64_t unit = (uint64_t)kMapSubs * kTile;                        // 4 KiB
-    // at most 8 states: every run of a part in one word, a lane per part (map_nib_kernel);
-    // else lane groups of 16 or 32 start states, two chains per lane up to 32 states
-    const bool nib = d->n_states <= 8;
-    const uint32_t groups = d->n_states <= 16 ? 2u : 1u;
+    // at most 16 states: every run of a part in one or two words, a lane per part
+    // (map_nib_kernel); else a lane per start state, two chains per lane up to 32 states
+    const bool nib = d->n_states <= kNibMaxStates;
+    const uint32_t groups = 1u;
     const uint32_t chains = d->n_states <= 32 ? 2u : 1u;
     const uint32_t parts = nib ? 1u : groups * chains;
     const int tab = d->d_pair ? TAB_PAIR : TAB_ONE;
@@ -807,17 +858,17 @@ int map_scan_impl(const dna_dfa *d, const uint8_t *seq, uint64_t len, cudaStream
     const size_t o_bound = positions ? take(nq * kMapSubs * 4) : 0;
     const size_t o_gstart = positions ? take((size_t)n_chunks * 32 * parts * 4) : 0;
     const size_t o_given = positions ? take((size_t)n_chunks * kMapSubs * 4) : 0;
-    const size_t o_cpre = positions && nib ? take((size_t)n_chunks * 8 * 4) : 0;
+    const size_t o_cpre = positions && nib ? take((size_t)n_chunks * kNibMaxStates * 4) : 0;
     const size_t o_bstart = positions && nib ? take((size_t)n_chunks * 4) : 0;
     const size_t optin = pr.smem_optin ? pr.smem_optin : 232448;
     const size_t part_tile = chains == 1 ? (size_t)kMapTile : (size_t)2048 / parts;
-    const size_t msmem = nib ? (size_t)kNibWarps * kStageBytesNib
+    const size_t msmem = nib ? kNibSmem
                              : (size_t)kMapWarps * 2 * parts * part_tile + (size_t)d->n_states * 16 + 2048 +
                                    (size_t)d->n_states * (tab == TAB_PAIR ? (size_t)kPairRowBytes : (size_t)kOneRowBytes);
-    void (*fn)(MapParams) = nib ? map_nib_kernel
+    void (*fn)(MapParams) = nib ? (d->n_states <= 8 ? map_nib_kernel<1> : map_nib_kernel<2>)
                           : tab == TAB_ONE ? map_kernel<1, TAB_ONE, 1>
                           : chains == 1 ? map_kernel<1, TAB_PAIR, 1>
-                          : groups == 2 ? map_kernel<2, TAB_PAIR, 2> : map_kernel<1, TAB_PAIR, 2>;
+                          : map_kernel<1, TAB_PAIR, 2>;
     // the kernel's static shared memory (its decoded rows, 3.5 KB per part) comes off the
     // block's shared memory before the dynamic part
     size_t static_smem = 0;

@@ -352,14 +352,15 @@ def _reset_heavy(seed, n, frac):
     return s
 
 
-@pytest.mark.parametrize("Q", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("Q", [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 15, 16])
 @pytest.mark.parametrize("n,offset", [(1, 3), (127, 0), (129, 5), (32 * 4096 - 1, 7), (32 * 4096 + 1, 1),
                                       (1 * MiB + 5, 11), (9 * MiB + 77, 2)])
 def test_nibble_chunk_maps_every_state_count(Q, n, offset):
-    """Automata of at most 8 states whose runs never meet keep every run of a part in
-    4-bit fields of one register. Every state count, an accepting start state, lengths
-    at part and row edges and unaligned starts: counts and positions equal the
-    oracle's."""
+    """Automata of at most 16 states whose runs never meet keep every run of a part in
+    4-bit fields of one register (8 states) or two (16 states, where each lookup picks
+    between the rows of states 0..7 and 8..15). Every state count, an accepting start
+    state, lengths at part and row edges and unaligned starts: counts and positions
+    equal the oracle's."""
     rng = np.random.default_rng(700 + Q)
     table = np.stack([rng.permutation(Q) for _ in range(4)], axis=1).astype(np.uint32)
     acc = (rng.random(Q) < 0.4).astype(np.uint8)
@@ -374,11 +375,12 @@ def test_nibble_chunk_maps_every_state_count(Q, n, offset):
     assert c2 == want_c
 
 
+@pytest.mark.parametrize("Q", [8, 16])
 @pytest.mark.parametrize("frac", [0.3, 0.6, 1.0])
-def test_nibble_chunk_maps_with_reset_bytes_in_most_rows(frac):
+def test_nibble_chunk_maps_with_reset_bytes_in_most_rows(frac, Q):
     """Rows with a reset byte take the one-symbol steps of the nibble kernel (every run
     back to q0, counted when q0 accepts); an all-N sequence resets every byte."""
-    table, acc = _permutation_automaton(8, 711)
+    table, acc = _permutation_automaton(Q, 711)
     acc[0] = 1
     n = 3 * MiB + 1234
     seq = np.full(n, ord("N"), dtype=np.uint8) if frac == 1.0 else _reset_heavy(712, n, frac)
