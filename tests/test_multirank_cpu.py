@@ -164,3 +164,47 @@ def test_gloo_ranks_join_one_sequence_split_across_them(tmp_path, world, kind, u
         assert all(int(x[4]) == 1 and int(x[5]) == 0 for x in rows)
     if kind == "counter":
         assert any(int(x[5]) > 0 for x in rows)   # some start was wrong and repaired
+
+
+def _tiny_join_worker(rank, world, port, out_path, n):
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t, a = _counter_table(3)
+        seq = np.frombuffer(b"AACANAAGTAA"[:n], dtype=np.uint8)
+        cuts = [n * r // world for r in range(world + 1)]
+        lo, hi = cuts[rank], cuts[rank + 1]
+
+        def scan_piece(q):
+            return oracle.run_piece(t, a, q, seq[lo:hi])
+
+        r = shard.scan_sharded(scan_piece, offset=lo, guess=(rank * 2) % 3)
+        with open(f"{out_path}.{rank}.txt", "w") as f:
+            f.write(f"{r['count']} {r['start']} {r['last']} {' '.join(str(x) for x in r['positions'])}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,n", [(4, 3), (4, 5), (3, 0)])
+def test_gloo_join_with_empty_pieces(tmp_path, world, n):
+    """Pieces may be empty (more ranks than bytes, or an empty sequence): an empty piece
+    ends where it starts, and the join still gives the whole run's count, positions and
+    every piece's true start."""
+    import oracle
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "tiny")
+    mp.start_processes(_tiny_join_worker, args=(world, _free_port(), out, n), nprocs=world, join=True,
+                       start_method="spawn")
+    t, a = _counter_table(3)
+    seq = np.frombuffer(b"AACANAAGTAA"[:n], dtype=np.uint8)
+    want_c, want_p = oracle.run(t, a, seq)
+    rows = [open(f"{out}.{r}.txt").read().split() for r in range(world)]
+    assert all(int(x[0]) == want_c for x in rows)
+    assert [int(v) for x in rows for v in x[3:]] == list(want_p)
+    cuts = [n * r // world for r in range(world + 1)]
+    for r in range(world):
+        assert int(rows[r][1]) == oracle.run_from(t, a, 0, seq[:cuts[r]])[1]
+        assert int(rows[r][2]) == oracle.run_from(t, a, 0, seq[:cuts[r + 1]])[1]
