@@ -555,6 +555,20 @@ def bench_plain_configs(dna, torch, stream, peak):
         "matches": int(cnt.item()), "chunk_maps": bool(dfa.info().chunk_maps), "output": "count",
         "note": "runs from different states never meet: every chunk is run from all 8 states, "
                 "held as 4-bit fields of one register per lane and moved by byte permutes"}
+    # 16 states whose runs never meet: every run as a 4-bit field of two registers per lane
+    rng = np.random.Generator(np.random.PCG64(16))
+    table = np.stack([rng.permutation(16) for _ in range(4)], axis=1).astype(np.uint32)
+    acc = (rng.random(16) < 0.25).astype(np.uint8)
+    acc[0] = 0
+    acc[int(rng.integers(1, 16))] = 1
+    dfa16 = dna.Dfa(table, dna.pack_accept(acc))
+    fn = lambda: dna.scan(dfa16, d, stream=stream, out_count=cnt)
+    ms = timed(fn, 10)
+    out["nonconverging_256MiB_perm16"] = {
+        "bytes": int(full.size), "ms_per_step": ms, "gbs": full.size / (ms * 1e-3) / 1e9,
+        "matches": int(cnt.item()), "chunk_maps": bool(dfa16.info().chunk_maps), "output": "count",
+        "note": "16 states whose runs never meet: every run a 4-bit field of two registers per lane; "
+                "each lookup picks between the rows of states 0-7 and 8-15"}
     # 64 states whose runs never meet: two warps per chunk, one per block of 32 start states
     rng = np.random.Generator(np.random.PCG64(64))
     table = np.stack([rng.permutation(64) for _ in range(4)], axis=1).astype(np.uint32)
