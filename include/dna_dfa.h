@@ -115,8 +115,9 @@ typedef struct {
 #define DNA_PLACE_SMEM_ONE   2  /* one-symbol table in shared memory */
 #define DNA_PLACE_GLOBAL_ONE 3  /* one-symbol table in global memory (L2 resident) */
 /* Chunk maps (automata of at most 256 states): each chunk is run from every state at once
- * (the possible starting states of Sec. III-A taken in full; a warp per 32 start states),
- * and a join composes the chunk maps in order. dfa_load picks it for automata whose runs
+ * (the possible starting states of Sec. III-A taken in full: up to 16 states as 4-bit
+ * fields of one or two registers per lane, else a warp per 32 start states), and a join
+ * composes the chunk maps in order. dfa_load picks it for automata whose runs
  * from different states do not meet within 16 symbols of random DNA (speculation would
  * rarely be repaired in the chunk's first bytes); it can also be requested through
  * dna_plan.placement. Larger automata whose runs never meet are scanned with speculation
@@ -186,7 +187,8 @@ int dfa_analyze(const uint32_t *table, uint32_t n_states, int32_t *definite_dept
  * can arise after the call returns except CUDA's own (reported by the stream).
  * Kernels: one chunk-scan kernel (speculation, chunk scan, join) and, with positions,
  * one extraction kernel; automata using chunk maps run a map kernel and a join kernel
- * first (and, with positions, the chunk-scan kernels from the exact chunk starts).
+ * first (and, with positions, a kernel giving every sub-chunk's start for automata of
+ * at most 16 states, then the chunk-scan kernels from the exact chunk starts).
  * Errors: DNA_ERR_INVALID_ARG (synchronous), DNA_ERR_NOMEM, DNA_ERR_CUDA,
  * DNA_ERR_CAPACITY (a plan's placement the automaton does not fit).
  */
