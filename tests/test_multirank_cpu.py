@@ -208,3 +208,40 @@ def test_gloo_join_with_empty_pieces(tmp_path, world, n):
     for r in range(world):
         assert int(rows[r][1]) == oracle.run_from(t, a, 0, seq[:cuts[r]])[1]
         assert int(rows[r][2]) == oracle.run_from(t, a, 0, seq[:cuts[r + 1]])[1]
+
+
+def _flaky_worker(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    calls = [0]
+
+    def scan_piece(q):
+        # a scanner whose last state changes on every call
+        calls[0] += 1
+        return 0, calls[0] * 7 + rank, None
+
+    try:
+        r = shard.scan_sharded(scan_piece, guess=1)
+        try:
+            shard.scan_sharded(lambda q: (0, 5, None), guess=1, max_rounds=1)
+            msg = "no error"
+        except RuntimeError as e:
+            msg = str(e)
+        with open(f"{out_path}.{rank}.txt", "w") as f:
+            f.write(f"{r['rounds']}|{msg}")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_join_rounds_are_bounded_and_a_round_limit_raises(tmp_path):
+    """Piece 0's start is fixed and a piece stops rescanning once its start is its left
+    neighbour's last state, so the starts settle within 'world' rounds whatever the
+    scanner returns; a round limit below what the starts need raises on every rank."""
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "flaky")
+    mp.start_processes(_flaky_worker, args=(3, _free_port(), out), nprocs=3, join=True, start_method="spawn")
+    rows = [open(f"{out}.{r}.txt").read().split("|") for r in range(3)]
+    assert all(int(x[0]) <= 3 for x in rows), rows
+    assert all("disagree after 1 rounds" in x[1] for x in rows), rows
