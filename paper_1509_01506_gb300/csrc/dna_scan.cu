@@ -102,10 +102,12 @@ __device__ __forceinline__ void stage_row(uint8_t *slot, const uint8_t *abase, u
 // state | accept after the first symbol << 30 | accept after the second << 31) and
 // writes the accepting positions from output index o. The walk itself has no branches:
 // the accept bits of the 128 positions collect in a 4-word mask, which is turned into
-// positions afterwards. Unless 'checked', the row is first tested for non-base bytes;
-// then it returns false (writing nothing) and the caller walks the row byte by byte.
+// positions afterwards. q and o leave as the state after the row and the next output
+// index (rescans continue from them). Unless 'checked', the row is first tested for
+// non-base bytes; then it returns false (writing nothing, q and o unchanged) and the
+// caller walks the row byte by byte.
 __device__ __forceinline__ bool walk_row_pairs(const EmitParams &p, const uint32_t *ptab, uint64_t rs,
-                                               uint32_t q, unsigned long long o, bool checked) {
+                                               uint32_t &q, unsigned long long &o, bool checked) {
     const uint4 *src = reinterpret_cast<const uint4 *>(p.abase + rs);
     if (!checked) {
         uint32_t err = 0;
@@ -385,9 +387,11 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             for (uint64_t rs = b; rs < to && (o < p.cap || lab); rs += kTile) {
                 uint32_t k0, k1;
                 row_span(rs, from, to, k0, k1);
-                // a whole row of bases: two symbols per lookup
+                // a whole row of bases: two symbols per lookup (without labels, the
+                // branch-free walk that writes the positions from the row's mask)
                 if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile &&
-                    walk_row_pairs_lab(p, ptab, rs, q, o, false, s_wlab + tid))
+                    (lab ? walk_row_pairs_lab(p, ptab, rs, q, o, false, s_wlab + tid)
+                         : walk_row_pairs(p, ptab, rs, q, o, false)))
                     continue;
                 q = walk_row(slot, rs, k0, k1, q, o);
             }
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(1024) emit_kernel(EmitParams p, uint32_t tab5_
             uint32_t q_row = rec[1];
             if (ptab_in_smem && k0 == 0 && k1 == (uint32_t)kTile &&
                 (lab ? walk_row_pairs_lab(p, ptab, rs, q_row, o, all_bases, s_wlab + tid)
-                     : walk_row_pairs(p, ptab, rs, rec[1], o, all_bases)))
+                     : walk_row_pairs(p, ptab, rs, q_row, o, all_bases)))
                 continue;
             walk_row(slot, rs, k0, k1, rec[1], o);
         }
