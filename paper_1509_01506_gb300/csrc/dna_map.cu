@@ -17,9 +17,10 @@
 // total count and every sub-chunk's exact start state. The positions come from the
 // single-sequence kernels run with those exact starts.
 //
-// Lookups never conflict in shared memory: every lane has its own copy of the table in
-// its own bank. Automata of up to about 90 states use the two-symbol table (2 KiB per
-// state); larger ones, up to kMaxMapStates, a one-symbol table (512 B per state).
+// Lookups never conflict in shared memory. The register-field kernels read 8-byte rows
+// of 128-byte tables (one row per symbol pair); the others give every lane its own copy
+// of the table in its own bank: the two-symbol table up to about 90 states (2 KiB per
+// state), a one-symbol table (512 B per state) up to kMaxMapStates.
 
 #include <cuda_runtime.h>
 
